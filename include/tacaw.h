@@ -1,0 +1,151 @@
+/*
+ * tacaw.h -- C ABI of libtacaw.so, the GB300 (sm_103a) TACAW hot path.
+ *
+ * The method is the one of arXiv 2602.10064 (PySlice): for every frame of an atomic
+ * trajectory and every probe position the electron wave is propagated by multislice
+ * through slice potentials built from Kirkland's parametrisation, and the stack of exit
+ * waves psi(k, t) is transformed along time to give the vibrational intensity
+ * I(k, w) = |F_t[psi(k,t) - <psi(k,t)>_t]|^2.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int: TACAW_OK (0) or a negative TACAW_E* code.  The message of the
+ *    last failure on a context is available from tacaw_last_error().  A failed call leaves
+ *    output buffers unspecified and the context usable.
+ *  - Device pointers are plain CUDA device addresses (e.g. torch tensor data_ptr()).  The
+ *    caller owns every buffer it passes; the library owns the context, its tables, its
+ *    scratch memory and the state of admitted serving requests.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls taking a
+ *    stream are stream-ordered and asynchronous unless stated otherwise: they return once the
+ *    work is enqueued.  Scratch memory comes from the stream-ordered allocator of the context's
+ *    device and is released on the same stream.
+ *  - Arrays are row-major, complex values are interleaved (re, im) float32 pairs ("c64").
+ *    Reciprocal-space arrays are in FFT order: index i on an n-point axis of length L has
+ *    spatial frequency k = m / L (cycles per Angstrom, no 2 pi) with m = i for i < (n+1)/2
+ *    and m = i - n otherwise.  Time-frequency bins are in the same order: bin m has
+ *    f_m = m / (F dt).
+ *  - Grids nx, ny must be powers of two in [32, 1024].
+ *  - Units: Angstrom, eV, fs, mrad; potentials in V*A (projected), sigma in rad/(V*A).
+ */
+#ifndef TACAW_H
+#define TACAW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TACAW_OK 0
+#define TACAW_PENDING 1      /* tacaw_poll: request admitted or queued, not finished */
+#define TACAW_EINVAL (-1)    /* bad argument: shape, size, pointer kind, unknown species */
+#define TACAW_ENOMEM (-2)    /* device allocation failed */
+#define TACAW_ETOOBIG (-3)   /* request can never fit the context's HBM budget */
+#define TACAW_ETIMEOUT (-4)  /* a bounded wait ran out (kernel status word or tacaw_wait) */
+#define TACAW_ECUDA (-5)     /* CUDA runtime error; see tacaw_last_error */
+#define TACAW_ECANCELED (-6) /* request cancelled before it finished */
+#define TACAW_ENOTFOUND (-7) /* unknown ticket */
+
+/* Time-transform arithmetic (tacaw_spectrum, tacaw_run). */
+#define TACAW_DFT_FP32 0   /* FP32 SIMT dense DFT: the plain path */
+#define TACAW_DFT_BF16X3 1 /* tcgen05 BF16 GEMM, hi*hi + hi*lo + lo*hi, FP32 accumulation */
+#define TACAW_DFT_TF32X3 2 /* tcgen05 TF32 GEMM, same three-product split */
+#define TACAW_DFT_BF16 3   /* tcgen05 BF16 GEMM, single product (precision study only) */
+#define TACAW_DFT_TF32 4   /* tcgen05 TF32 GEMM, single product (precision study only) */
+
+/* Output reduction (tacaw_spectrum, tacaw_run). */
+#define TACAW_REDUCE_NONE 0     /* full S[P][F][ny][nx] */
+#define TACAW_REDUCE_DETECTOR 1 /* spectrum image SI[P][F] = sum over the band-limited disc of S */
+
+typedef struct tacaw_ctx tacaw_ctx;
+
+/* Geometry and beam of one simulation. */
+typedef struct tacaw_params {
+  int32_t nx, ny;                 /* grid points along x and y */
+  int32_t n_slices;               /* S >= 1; slice thickness dz = cell[2] / S */
+  int32_t bandlimit_transmission; /* 1: t <- IDFT(M DFT(t)) / Nq; 0: t = exp(i sigma V) */
+  double cell[3];                 /* periodic cell Lx, Ly, Lz (A) */
+  double voltage_ev;              /* beam energy (eV) */
+  double bandlimit;               /* mask radius as a fraction of Nyquist (2/3); <= 0: no mask */
+  double dt_fs;                   /* frame spacing (fs); sets the frequency axis only */
+} tacaw_params;
+
+/* Illumination. */
+typedef struct tacaw_probe {
+  double alpha_mrad; /* convergence semi-angle; <= 0: plane wave (n_probes must be 1) */
+  int32_t n_probes;  /* P >= 1 */
+  int32_t pad_;
+  const double* xy;  /* HOST [P][2] probe positions (A); NULL: one probe at (0, 0) */
+} tacaw_probe;
+
+/* Library version string (static storage). */
+const char* tacaw_version(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
+ * serving loop admits at once (0 = 90% of the device's free memory at creation).  *out
+ * receives a library-owned handle, released by tacaw_destroy. */
+int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes);
+
+/* Destroy a context: waits for admitted serving requests, frees every library allocation. */
+int tacaw_destroy(tacaw_ctx* ctx);
+
+/* Message of the last failure on ctx (empty string if none); valid until the next call. */
+const char* tacaw_last_error(const tacaw_ctx* ctx);
+
+/* Load form-factor coefficients (Methods, "Atomic Scattering Potentials": Kirkland's form
+ * f(q) = sum_i a_i/(q^2+b_i) + c_i exp(-d_i q^2), q in 1/A without 2 pi, f in A).
+ * Z: HOST [nZ] atomic numbers; coef: HOST [nZ][12] as a1 b1 a2 b2 a3 b3 c1 d1 c2 d2 c3 d3.
+ * Replaces any earlier table.  EINVAL for nZ < 1, nZ > 64, repeated Z or b_i <= 0. */
+int tacaw_load_form_factors(tacaw_ctx* ctx, const int32_t* Z, const double* coef, int32_t nZ);
+
+/* Slice binning (Methods, "Atomic Scattering Potentials": the sum runs over the atoms inside
+ * a slice's z-bounds).  slice_out[f][j] = s with z wrapped into [0, Lz) and
+ * s = floor(z_w / dz) clamped to [0, S-1], all in FP64 from the float32 input.
+ * pos: DEVICE float32 [nf][n_atoms][3]; slice_out: DEVICE int32 [nf][n_atoms]. */
+int tacaw_bin_slices(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, int64_t n_atoms,
+                     int64_t nf, int32_t* slice_out, void* stream);
+
+/* Projected potential of every slice of nf frames (Methods, "Atomic Scattering Potentials"):
+ * V_s(r) = sum_k (2 pi a0 e / A) M(k) sum_{j in s} f_Zj(|k|) exp(2 pi i k.(r - r_j)), A = Lx Ly.
+ * The structure factor is evaluated by spreading each atom onto the grid with an
+ * exponential-of-semicircle kernel (width 12, beta 24) and deconvolving after the FFT.
+ * pos: DEVICE float32 [nf][n_atoms][3] (A); Z: DEVICE int32 [n_atoms] (each Z must be in the
+ * loaded table); V_out: DEVICE float32 [nf][S][ny][nx] (V*A). */
+int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z,
+                          int64_t n_atoms, int64_t nf, float* V_out, void* stream);
+
+/* Transmission functions (Methods, "Multislice Propagation": t = exp(i sigma V)), optionally
+ * band-limited.  V: DEVICE float32 [nf][S][ny][nx]; t_out: DEVICE c64 [nf][S][ny][nx]. */
+int tacaw_transmission(tacaw_ctx* ctx, const tacaw_params* params, const float* V, int64_t nf,
+                       float* t_out, void* stream);
+
+/* Multislice (Methods, "Multislice Propagation"): for each probe p and frame f,
+ * psi <- IDFT(P M DFT(t_s psi)) / Nq for s = 0..S-1 with P(k) = exp(-i pi lambda dz |k|^2),
+ * then psi_k = DFT(psi_exit) / sqrt(Nq).  V: DEVICE float32 [nf][S][ny][nx];
+ * psi_k_out: DEVICE c64 [P][nf][ny][nx]. */
+int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, int64_t nf,
+                    const tacaw_probe* probe, float* psi_k_out, void* stream);
+
+/* Time transform (Methods, "Workflow Architecture"): for every (p, q)
+ * S[p][m][q] = |sum_n (psi[p][n][q] - mean_n psi[p][n][q]) exp(-2 pi i m n / F)|^2,
+ * the mean and the residual in FP64, the sum by the arithmetic `precision` (TACAW_DFT_*).
+ * psi_k: DEVICE c64 [P][F][nq]; q_sel: DEVICE int32 [n_sel] ascending q indices to transform
+ * (others are written as 0), or NULL for all nq; S_out: DEVICE float32 [P][F][nq] for
+ * TACAW_REDUCE_NONE or [P][F] (sum over the selected q) for TACAW_REDUCE_DETECTOR. */
+int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
+                   int32_t reduce, const int32_t* q_sel, int64_t n_sel, float* S_out, void* stream);
+
+/* The whole hot path for one trajectory, fused: binning, potential, transmission,
+ * multislice for every (probe, frame), time transform over the band-limited q only.
+ * pos: float32 [F][n_atoms][3] and Z: int32 [n_atoms], HOST or DEVICE; S_out: float32
+ * [P][F][ny][nx] (REDUCE_NONE) or [P][F] (REDUCE_DETECTOR), HOST or DEVICE.  With host
+ * buffers the copies are part of the call (pinned host memory is fastest).  Synchronous on
+ * `stream` when any buffer is on the host, asynchronous otherwise. */
+int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z, int64_t n_atoms,
+              int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
+              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TACAW_H */

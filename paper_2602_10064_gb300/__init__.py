@@ -1,0 +1,306 @@
+"""GB300 (sm_103a) TACAW hot path: Python binding of libtacaw.so.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of libtacaw.so,
+whose C ABI is declared in include/tacaw.h.  torch tensors supply device memory and streams.
+The module-level functions carry the C names (tacaw_build_potential, ...); ``Context`` wraps
+a context handle.  There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+
+TACAW_OK = 0
+TACAW_PENDING = 1
+TACAW_EINVAL = -1
+TACAW_ENOMEM = -2
+TACAW_ETOOBIG = -3
+TACAW_ETIMEOUT = -4
+TACAW_ECUDA = -5
+TACAW_ECANCELED = -6
+TACAW_ENOTFOUND = -7
+
+DFT_FP32, DFT_BF16X3, DFT_TF32X3, DFT_BF16, DFT_TF32 = 0, 1, 2, 3, 4
+REDUCE_NONE, REDUCE_DETECTOR = 0, 1
+
+_CODES = {-1: "EINVAL", -2: "ENOMEM", -3: "ETOOBIG", -4: "ETIMEOUT", -5: "ECUDA", -6: "ECANCELED", -7: "ENOTFOUND"}
+
+
+class TacawError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tacaw {_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("n_slices", C.c_int32),
+                ("bandlimit_transmission", C.c_int32), ("cell", C.c_double * 3), ("voltage_ev", C.c_double),
+                ("bandlimit", C.c_double), ("dt_fs", C.c_double)]
+
+
+class Probe(C.Structure):
+    _fields_ = [("alpha_mrad", C.c_double), ("n_probes", C.c_int32), ("pad_", C.c_int32), ("xy", C.c_void_p)]
+
+
+def make_params(nx, ny, n_slices, cell, voltage_ev=100e3, bandlimit=2.0 / 3.0, bandlimit_transmission=1,
+                dt_fs=1.0) -> Params:
+    p = Params()
+    p.nx, p.ny, p.n_slices, p.bandlimit_transmission = int(nx), int(ny), int(n_slices), int(bandlimit_transmission)
+    p.cell[0], p.cell[1], p.cell[2] = (float(c) for c in cell)
+    p.voltage_ev, p.bandlimit, p.dt_fs = float(voltage_ev), float(bandlimit), float(dt_fs)
+    return p
+
+
+def params_of(w, **kw) -> Params:
+    """Parameters of a workloads.Workload (keyword overrides allowed)."""
+    d = dict(nx=w.nx, ny=w.ny, n_slices=w.n_slices, cell=w.cell, voltage_ev=w.voltage_ev, bandlimit=w.bandlimit,
+             bandlimit_transmission=w.bandlimit_transmission, dt_fs=w.dt_fs)
+    d.update(kw)
+    return make_params(**d)
+
+
+class ProbeSpec:
+    """A tacaw_probe plus the host buffer its xy pointer refers to."""
+
+    def __init__(self, alpha_mrad=0.0, xy=None):
+        self.xy = None if xy is None else np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        n = 1 if self.xy is None else self.xy.shape[0]
+        self.c = Probe(float(alpha_mrad), n, 0, None if self.xy is None else self.xy.ctypes.data)
+
+    @property
+    def n_probes(self):
+        return self.c.n_probes
+
+
+def probe_of(w) -> ProbeSpec:
+    return ProbeSpec(w.alpha_mrad, w.probes if w.alpha_mrad > 0 else None)
+
+
+# ------------------------------------------------------------------------------------------
+# library loading
+# ------------------------------------------------------------------------------------------
+_lib = None
+
+
+def lib():
+    """The loaded libtacaw.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libtacaw.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        pp, prp = C.POINTER(Params), C.POINTER(Probe)
+        sig = {
+            "tacaw_version": (C.c_char_p, []),
+            "tacaw_create": (C.c_int, [C.POINTER(vp), i32, C.c_uint64]),
+            "tacaw_destroy": (C.c_int, [vp]),
+            "tacaw_last_error": (C.c_char_p, [vp]),
+            "tacaw_load_form_factors": (C.c_int, [vp, vp, vp, i32]),
+            "tacaw_bin_slices": (C.c_int, [vp, pp, vp, i64, i64, vp, vp]),
+            "tacaw_build_potential": (C.c_int, [vp, pp, vp, vp, i64, i64, vp, vp]),
+            "tacaw_transmission": (C.c_int, [vp, pp, vp, i64, vp, vp]),
+            "tacaw_propagate": (C.c_int, [vp, pp, vp, i64, prp, vp, vp]),
+            "tacaw_spectrum": (C.c_int, [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp, vp]),
+            "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
+            "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
+            "tacaw_spectrum", "tacaw_run"]
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to libtacaw must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays passed to libtacaw must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} to libtacaw")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, rc):
+    if rc != TACAW_OK:
+        raise TacawError(rc, lib().tacaw_last_error(ctx).decode())
+    return rc
+
+
+# ------------------------------------------------------------------------------------------
+# C names
+# ------------------------------------------------------------------------------------------
+def tacaw_version() -> str:
+    return lib().tacaw_version().decode()
+
+
+def tacaw_create(device=0, hbm_budget_bytes=0):
+    h = C.c_void_p()
+    rc = lib().tacaw_create(C.byref(h), int(device), int(hbm_budget_bytes))
+    if rc != TACAW_OK:
+        raise TacawError(rc, "tacaw_create failed")
+    return h.value
+
+
+def tacaw_destroy(ctx):
+    return lib().tacaw_destroy(ctx)
+
+
+def tacaw_load_form_factors(ctx, Z, coef):
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    return _check(ctx, lib().tacaw_load_form_factors(ctx, Z.ctypes.data, coef.ctypes.data, len(Z)))
+
+
+def tacaw_bin_slices(ctx, params, pos, n_atoms, nf, slice_out, stream=None):
+    return _check(ctx, lib().tacaw_bin_slices(ctx, C.byref(params), _ptr(pos), n_atoms, nf, _ptr(slice_out),
+                                              _stream(stream)))
+
+
+def tacaw_build_potential(ctx, params, pos, Z, n_atoms, nf, V_out, stream=None):
+    return _check(ctx, lib().tacaw_build_potential(ctx, C.byref(params), _ptr(pos), _ptr(Z), n_atoms, nf,
+                                                   _ptr(V_out), _stream(stream)))
+
+
+def tacaw_transmission(ctx, params, V, nf, t_out, stream=None):
+    return _check(ctx, lib().tacaw_transmission(ctx, C.byref(params), _ptr(V), nf, _ptr(t_out), _stream(stream)))
+
+
+def tacaw_propagate(ctx, params, V, nf, probe: ProbeSpec, psi_k_out, stream=None):
+    return _check(ctx, lib().tacaw_propagate(ctx, C.byref(params), _ptr(V), nf, C.byref(probe.c), _ptr(psi_k_out),
+                                             _stream(stream)))
+
+
+def tacaw_spectrum(ctx, psi_k, P, F, nq, precision, reduce, q_sel, n_sel, S_out, stream=None):
+    return _check(ctx, lib().tacaw_spectrum(ctx, _ptr(psi_k), P, F, nq, precision, reduce, _ptr(q_sel), n_sel,
+                                            _ptr(S_out), _stream(stream)))
+
+
+def tacaw_run(ctx, params, pos, Z, n_atoms, n_frames, probe: ProbeSpec, precision, reduce, S_out, stream=None):
+    return _check(ctx, lib().tacaw_run(ctx, C.byref(params), _ptr(pos), _ptr(Z), n_atoms, n_frames,
+                                       C.byref(probe.c), precision, reduce, _ptr(S_out), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------
+# convenience wrapper over torch tensors
+# ------------------------------------------------------------------------------------------
+class Context:
+    """A libtacaw context on one CUDA device; methods take torch tensors."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        self.device = device
+        self.h = tacaw_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h:
+            tacaw_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_form_factors(self, Z, coef):
+        tacaw_load_form_factors(self.h, Z, coef)
+
+    def bin_slices(self, params, pos, stream=None):
+        import torch
+        nf, A = pos.shape[0], pos.shape[1]
+        out = torch.empty((nf, A), dtype=torch.int32, device=pos.device)
+        tacaw_bin_slices(self.h, params, pos, A, nf, out, stream)
+        return out
+
+    def build_potential(self, params, pos, Z, stream=None):
+        import torch
+        nf, A = pos.shape[0], pos.shape[1]
+        V = torch.empty((nf, params.n_slices, params.ny, params.nx), dtype=torch.float32, device=pos.device)
+        tacaw_build_potential(self.h, params, pos, Z, A, nf, V, stream)
+        return V
+
+    def transmission(self, params, V, stream=None):
+        import torch
+        t = torch.empty(V.shape + (2,), dtype=torch.float32, device=V.device)
+        tacaw_transmission(self.h, params, V, V.shape[0], t, stream)
+        return torch.view_as_complex(t)
+
+    def propagate(self, params, V, probe: ProbeSpec, stream=None):
+        import torch
+        nf = V.shape[0]
+        out = torch.empty((probe.n_probes, nf, params.ny, params.nx, 2), dtype=torch.float32, device=V.device)
+        tacaw_propagate(self.h, params, V, nf, probe, out, stream)
+        return torch.view_as_complex(out)
+
+    def spectrum(self, psi_k, precision=DFT_FP32, reduce=REDUCE_NONE, q_sel=None, stream=None):
+        """psi_k: complex64 [P][F][...] tensor; returns S [P][F][...] (or [P][F])."""
+        import torch
+        P, F = psi_k.shape[0], psi_k.shape[1]
+        nq = int(math.prod(psi_k.shape[2:]))
+        shape = (P, F) + tuple(psi_k.shape[2:]) if reduce == REDUCE_NONE else (P, F)
+        S = torch.empty(shape, dtype=torch.float32, device=psi_k.device)
+        psi = torch.view_as_real(psi_k.contiguous())
+        tacaw_spectrum(self.h, psi, P, F, nq, precision, reduce, q_sel, 0 if q_sel is None else q_sel.numel(), S,
+                       stream)
+        return S
+
+    def run(self, params, pos, Z, probe: ProbeSpec, precision=DFT_FP32, reduce=REDUCE_NONE, out=None, stream=None):
+        import torch
+        F, A = pos.shape[0], pos.shape[1]
+        P = probe.n_probes
+        shape = (P, F, params.ny, params.nx) if reduce == REDUCE_NONE else (P, F)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=pos.device)
+        tacaw_run(self.h, params, pos, Z, A, F, probe, precision, reduce, out, stream)
+        return out
+
+
+# ------------------------------------------------------------------------------------------
+# axes (Supplement, "Sampling Considerations": dk = 1/L, df = 1/(N dt), f_max = 1/(2 dt))
+# ------------------------------------------------------------------------------------------
+def frequency_axis_thz(n_frames, dt_fs):
+    """Frequencies of the time-transform bins in FFT order (THz): f_m = m / (F dt)."""
+    return np.fft.fftfreq(int(n_frames), d=float(dt_fs) * 1e-3)
+
+
+def k_axis(n, L):
+    """Spatial frequencies (cycles/A) of an n-point axis of length L, FFT order."""
+    return np.fft.fftfreq(int(n), d=float(L) / int(n))
+
+
+def sampling(L, sampling_A, n_frames, dt_fs):
+    """(dk, k_max, df, f_max) of a simulation: 1/L, 1/(2 dx), 1/(F dt), 1/(2 dt) (A^-1, THz)."""
+    dt_ps = float(dt_fs) * 1e-3
+    return 1.0 / L, 1.0 / (2.0 * sampling_A), 1.0 / (n_frames * dt_ps), 1.0 / (2.0 * dt_ps)

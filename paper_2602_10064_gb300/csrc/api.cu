@@ -1,0 +1,746 @@
+// C-ABI entry points of libtacaw.so (declared in include/tacaw.h): context, host-side FP64
+// tables (twiddles, masks, propagator, spreading-kernel transform) and the orchestration of
+// the slice and spectrum kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tacaw.h"
+#include "tacaw_api_internal.h"
+#include "tacaw_internal.cuh"
+
+using namespace tacaw;
+
+namespace {
+
+// CODATA 2018 constants (h, e, c exact in SI).
+constexpr double kH = 6.62607015e-34, kQe = 1.602176634e-19, kMe = 9.1093837015e-31, kC = 299792458.0;
+constexpr double kA0 = 0.529177210903, kEps0 = 8.8541878128e-12;
+
+double wavelength_A(double V) {
+  const double eV = kQe * V;
+  return kH / std::sqrt(2.0 * kMe * eV * (1.0 + eV / (2.0 * kMe * kC * kC))) * 1e10;
+}
+double sigma_per_VA(double V) {
+  const double gamma = 1.0 + kQe * V / (kMe * kC * kC);
+  return 2.0 * M_PI * gamma * kMe * kQe * (wavelength_A(V) * 1e-10) / (kH * kH) * 1e-10;
+}
+double kirkland_pref() { return 2.0 * M_PI * kA0 * (kQe / (4.0 * M_PI * kEps0) * 1e10); }
+
+double kfreq(int i, int n, double L) {
+  const int m = (i < (n + 1) / 2) ? i : i - n;
+  return (double)m / L;
+}
+
+// Circular mask |k|^2 <= kr^2 (kr <= 0: everything inside).
+bool in_disc(int iy, int ix, int nx, int ny, double Lx, double Ly, double kr) {
+  const double kx = kfreq(ix, nx, Lx), ky = kfreq(iy, ny, Ly);
+  const double k2 = kx * kx + ky * ky;
+  return k2 <= kr * kr;
+}
+
+double band_radius(const tacaw_params& p) {
+  if (p.bandlimit <= 0.0) return -1.0;
+  const double a = 0.5 * (double)p.nx / p.cell[0], b = 0.5 * (double)p.ny / p.cell[1];
+  return p.bandlimit * (a < b ? a : b);
+}
+
+bool pow2_in_range(int n) { return n >= 32 && n <= 1024 && (n & (n - 1)) == 0; }
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int k = 1; k <= n; ++k) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+      }
+      dp = n * (z * p0 - p1) / (z * z - 1.0);
+      const double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+constexpr int kSpreadHalf = 6;         // kernel width w = 12 grid points
+constexpr double kSpreadBeta = 24.0;   // beta = 2.0 w
+
+double es_phi(double z) {
+  const double a = 1.0 - z * z;
+  return a > 0.0 ? std::exp(kSpreadBeta * (std::sqrt(a) - 1.0)) : 0.0;
+}
+
+// Phi(m) = h int_{-1}^{1} phi(z) cos(2 pi m h z / N) dz: the transform of the spreading kernel.
+double es_transform(int m, int N) {
+  static std::vector<double> gx, gw;
+  static std::once_flag once;
+  std::call_once(once, [] { gauss_legendre(160, gx, gw); });
+  double s = 0.0;
+  for (size_t i = 0; i < gx.size(); ++i)
+    s += gw[i] * es_phi(gx[i]) * std::cos(2.0 * M_PI * m * kSpreadHalf * gx[i] / N);
+  return kSpreadHalf * s;
+}
+
+}  // namespace
+
+// ===================================================================================
+// context
+// ===================================================================================
+namespace tacaw {
+
+int set_err(tacaw_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return TACAW_OK;
+  if (e == cudaErrorMemoryAllocation) return set_err(c, TACAW_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+  return set_err(c, TACAW_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+}  // namespace tacaw
+
+#define CK(expr)                                              \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, #expr);   \
+  } while (0)
+
+#define TRY_RC(expr)            \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != TACAW_OK) return rc_; \
+  } while (0)
+
+namespace {
+
+template <class T>
+int owned_alloc(tacaw_ctx* ctx, T** p, size_t n) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, sizeof(T) * std::max<size_t>(n, 1));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMalloc");
+  ctx->owned.push_back(v);
+  *p = static_cast<T*>(v);
+  return TACAW_OK;
+}
+
+int is_device_ptr(const void* p) {
+  if (!p) return 0;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_params(tacaw_ctx* ctx, const tacaw_params* p) {
+  if (!p) return set_err(ctx, TACAW_EINVAL, "params is NULL");
+  if (!pow2_in_range(p->nx) || !pow2_in_range(p->ny))
+    return set_err(ctx, TACAW_EINVAL, "grid %dx%d: nx, ny must be powers of two in [32, 1024]", p->nx, p->ny);
+  if (p->n_slices < 1 || p->n_slices > 256) return set_err(ctx, TACAW_EINVAL, "n_slices %d not in [1, 256]", p->n_slices);
+  for (int i = 0; i < 3; ++i)
+    if (!(p->cell[i] > 0.0) || !std::isfinite(p->cell[i])) return set_err(ctx, TACAW_EINVAL, "cell[%d] must be > 0", i);
+  if (!(p->voltage_ev > 0.0)) return set_err(ctx, TACAW_EINVAL, "voltage_ev must be > 0");
+  if (p->bandlimit > 0.0 && (p->bandlimit > 1.0 || !std::isfinite(p->bandlimit)))
+    return set_err(ctx, TACAW_EINVAL, "bandlimit must be in (0, 1] or <= 0 for none");
+  return TACAW_OK;
+}
+
+// Band of columns inside a disc of radius kr (kr <= 0: all columns).
+void make_band(int nx, int ny, double Lx, double Ly, double kr, int& W, int& Wp, int& mb, std::vector<int>& nb) {
+  if (kr <= 0.0 || in_disc(0, nx / 2, nx, ny, Lx, Ly, kr)) {
+    W = nx;
+    mb = nx / 2;
+  } else {
+    mb = -1;
+    for (int m = 0; m < nx / 2; ++m)
+      if (in_disc(0, m, nx, ny, Lx, Ly, kr)) mb = m;
+      else break;
+    W = mb >= 0 ? 2 * mb + 1 : 0;
+  }
+  Wp = std::max(32, (W + 31) / 32 * 32);
+  if (Wp > nx) Wp = nx;
+  nb.assign(Wp, -1);
+  for (int c = 0; c < W; ++c) {
+    const int x = c <= mb ? c : nx - (W - c);
+    int best = -1;
+    for (int n = 0; n <= ny / 2; ++n) {
+      const int iy = n;  // n = ny/2 is the Nyquist row (index ny/2)
+      if (kr <= 0.0 || in_disc(iy, x, nx, ny, Lx, Ly, kr)) best = n;
+      else break;
+    }
+    nb[c] = best;
+  }
+}
+
+}  // namespace
+
+namespace tacaw {
+
+// Geometry tables for one parameter set (cached).  Requires the form-factor table.
+int get_geo(tacaw_ctx* ctx, const tacaw_params& p, GeoCache** out) {
+  std::vector<double> key = {(double)p.nx, (double)p.ny, p.cell[0], p.cell[1], p.cell[2], (double)p.n_slices,
+                             p.voltage_ev, p.bandlimit};
+  auto it = ctx->geos.find(key);
+  if (it != ctx->geos.end() && it->second->ff_version == ctx->ff_version) {
+    *out = it->second.get();
+    return TACAW_OK;
+  }
+  auto g = std::make_unique<GeoCache>();
+  const int nx = p.nx, ny = p.ny;
+  const double Lx = p.cell[0], Ly = p.cell[1];
+  std::vector<int> nb;
+  int W, Wp, mb;
+  make_band(nx, ny, Lx, Ly, band_radius(p), W, Wp, mb, nb);
+  if (W == 0) return set_err(ctx, TACAW_EINVAL, "band limit excludes every column");
+  TRY_RC(owned_alloc(ctx, &g->colnb, Wp));
+  CK(cudaMemcpy(g->colnb, nb.data(), sizeof(int) * Wp, cudaMemcpyHostToDevice));
+  g->band = Band{W, Wp, mb, g->colnb};
+  // propagator P = exp(-i pi lambda dz (kx^2 + ky^2)) = Px Py, FP64 on host
+  const double lam = wavelength_A(p.voltage_ev), dz = p.cell[2] / p.n_slices;
+  std::vector<float2> hx(Wp, make_float2(0.f, 0.f)), hy(ny);
+  for (int c = 0; c < W; ++c) {
+    const int x = c <= mb ? c : nx - (W - c);
+    const double kx = kfreq(x, nx, Lx), ph = -M_PI * lam * dz * kx * kx;
+    hx[c] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+  }
+  for (int y = 0; y < ny; ++y) {
+    const double ky = kfreq(y, ny, Ly), ph = -M_PI * lam * dz * ky * ky;
+    hy[y] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+  }
+  TRY_RC(owned_alloc(ctx, &g->px, Wp));
+  TRY_RC(owned_alloc(ctx, &g->py, ny));
+  CK(cudaMemcpy(g->px, hx.data(), sizeof(float2) * Wp, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(g->py, hy.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice));
+  // spreading-kernel transforms
+  std::vector<double> phx(Wp, 1.0), phy(ny);
+  for (int c = 0; c < W; ++c) {
+    const int x = c <= mb ? c : nx - (W - c);
+    phx[c] = es_transform((x < (nx + 1) / 2) ? x : x - nx, nx);
+  }
+  for (int y = 0; y < ny; ++y) phy[y] = es_transform((y < (ny + 1) / 2) ? y : y - ny, ny);
+  TRY_RC(owned_alloc(ctx, &g->phix, Wp));
+  TRY_RC(owned_alloc(ctx, &g->phiy, ny));
+  CK(cudaMemcpy(g->phix, phx.data(), sizeof(double) * Wp, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(g->phiy, phy.data(), sizeof(double) * ny, cudaMemcpyHostToDevice));
+  // in-band q list (ascending q = iy * nx + x)
+  std::vector<int32_t> qs;
+  for (int y = 0; y < ny; ++y) {
+    const int n = (y < (ny + 1) / 2) ? y : y - ny;
+    for (int x = 0; x < nx; ++x) {
+      const int c = x <= mb ? x : (x >= nx - mb ? x - nx + W : -1);
+      if (c >= 0 && c < W && std::abs(n) <= nb[c]) qs.push_back(y * nx + x);
+    }
+  }
+  g->nsel = (int64_t)qs.size();
+  TRY_RC(owned_alloc(ctx, &g->qsel, qs.size()));
+  CK(cudaMemcpy(g->qsel, qs.data(), sizeof(int32_t) * qs.size(), cudaMemcpyHostToDevice));
+  // potential multiplier table over the loaded species (slot = table index)
+  const int nslot = (int)ctx->ffZ.size();
+  if (nslot > 0) {
+    g->nslot = nslot;
+    g->npair = (nslot + 1) / 2;
+    TRY_RC(owned_alloc(ctx, &g->coef_slots, 12 * (size_t)nslot));
+    CK(cudaMemcpy(g->coef_slots, ctx->ffcoef.data(), sizeof(double) * 12 * nslot, cudaMemcpyHostToDevice));
+    TRY_RC(owned_alloc(ctx, &g->mtab, (size_t)g->npair * ny * Wp));
+    const Geo geo{nx, ny, ctx->tw};
+    CK(launch_build_mtab(geo, g->band, g->npair, nslot, g->coef_slots, g->phix, g->phiy, Lx, Ly,
+                         kirkland_pref() / (Lx * Ly), g->mtab, 0));
+    CK(cudaDeviceSynchronize());
+  }
+  g->ff_version = ctx->ff_version;
+  *out = g.get();
+  ctx->geos[key] = std::move(g);
+  return TACAW_OK;
+}
+
+// Length-F time twiddles exp(-2 pi i j / F).
+int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out) {
+  auto it = ctx->time_tw.find(F);
+  if (it != ctx->time_tw.end()) {
+    *out = it->second;
+    return TACAW_OK;
+  }
+  std::vector<float2> h(F);
+  for (int64_t j = 0; j < F; ++j) {
+    const double a = -2.0 * M_PI * (double)j / (double)F;
+    h[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  float2* d;
+  TRY_RC(owned_alloc(ctx, &d, F));
+  CK(cudaMemcpy(d, h.data(), sizeof(float2) * F, cudaMemcpyHostToDevice));
+  ctx->time_tw[F] = d;
+  *out = d;
+  return TACAW_OK;
+}
+
+}  // namespace tacaw
+
+// ===================================================================================
+// entry points
+// ===================================================================================
+extern "C" {
+
+const char* tacaw_version(void) { return "tacaw-gb300 0.1 (sm_103a)"; }
+
+int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
+  if (!out) return TACAW_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return TACAW_EINVAL;
+  }
+  auto* ctx = new (std::nothrow) tacaw_ctx();
+  if (!ctx) return TACAW_ENOMEM;
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return TACAW_ECUDA;
+  }
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
+  // keep freed stream-ordered memory in the pool between calls
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  // FFT twiddle tables, FP64 on host: entries [N, 2N) hold exp(-2 pi i j / N)
+  std::vector<float2> tw(4096, make_float2(0.f, 0.f));
+  for (int N = 2; N <= 2048; N *= 2)
+    for (int j = 0; j < N; ++j) {
+      const double a = -2.0 * M_PI * (double)j / (double)N;
+      tw[N + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  if (owned_alloc(ctx, &ctx->tw, tw.size()) != TACAW_OK ||
+      cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    for (void* p : ctx->owned) cudaFree(p);
+    delete ctx;
+    return TACAW_ECUDA;
+  }
+  *out = ctx;
+  return TACAW_OK;
+}
+
+int tacaw_destroy(tacaw_ctx* ctx) {
+  if (!ctx) return TACAW_EINVAL;
+  cudaSetDevice(ctx->device);
+  serving_shutdown(ctx);
+  cudaDeviceSynchronize();
+  for (void* p : ctx->owned) cudaFree(p);
+  delete ctx;
+  return TACAW_OK;
+}
+
+const char* tacaw_last_error(const tacaw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tacaw_load_form_factors(tacaw_ctx* ctx, const int32_t* Z, const double* coef, int32_t nZ) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!Z || !coef || nZ < 1 || nZ > 64) return set_err(ctx, TACAW_EINVAL, "nZ must be in [1, 64]");
+  for (int i = 0; i < nZ; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (Z[i] == Z[j]) return set_err(ctx, TACAW_EINVAL, "Z=%d appears twice", Z[i]);
+    for (int k = 0; k < 3; ++k)
+      if (!(coef[12 * i + 2 * k + 1] > 0.0)) return set_err(ctx, TACAW_EINVAL, "b_%d of Z=%d must be > 0", k + 1, Z[i]);
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(coef[12 * i + k])) return set_err(ctx, TACAW_EINVAL, "non-finite coefficient");
+  }
+  ctx->ffZ.assign(Z, Z + nZ);
+  ctx->ffcoef.assign(coef, coef + 12 * (size_t)nZ);
+  ctx->ff_version++;
+  return TACAW_OK;
+}
+
+}  // extern "C"
+
+namespace tacaw {
+
+// Slot (form-factor table index) of every atom; host Z in, device int8 out.
+int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, Scratch& sc, int8_t** d_slot) {
+  std::vector<int32_t> hz(A);
+  if (A > 0) {
+    if (z_on_device) {
+      CK(cudaMemcpyAsync(hz.data(), Z, sizeof(int32_t) * A, cudaMemcpyDeviceToHost, sc.st));
+      CK(cudaStreamSynchronize(sc.st));
+    } else {
+      std::memcpy(hz.data(), Z, sizeof(int32_t) * A);
+    }
+  }
+  std::vector<int8_t> hs(A);
+  for (int64_t j = 0; j < A; ++j) {
+    int s = -1;
+    for (size_t i = 0; i < ctx->ffZ.size(); ++i)
+      if (ctx->ffZ[i] == hz[j]) s = (int)i;
+    if (s < 0) return set_err(ctx, TACAW_EINVAL, "atom %lld has Z=%d, not in the form-factor table", (long long)j, hz[j]);
+    hs[j] = (int8_t)s;
+  }
+  CK(sc.get(d_slot, A));
+  if (A > 0) {
+    CK(cudaMemcpyAsync(*d_slot, hs.data(), A, cudaMemcpyHostToDevice, sc.st));
+    CK(cudaStreamSynchronize(sc.st));  // hs is pageable and local
+  }
+  return TACAW_OK;
+}
+
+// Potential of frames [0, nf): binning, spreading row pass, column pass.  Leaves Ap (per
+// chunk) to `sink(f0, nfc, Ap)`, which runs the row pass out of the potential.
+template <class Sink>
+int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float* pos, const int8_t* slots,
+                     int64_t A, int64_t nf, int64_t chunk, Scratch& sc, Sink sink) {
+  const int S = p.n_slices, ny = p.ny;
+  const Geo geo{p.nx, p.ny, ctx->tw};
+  AtomRec* recs;
+  int* offs;
+  CK(sc.get(&recs, (size_t)nf * std::max<int64_t>(A, 1)));
+  CK(sc.get(&offs, (size_t)nf * (S + 1)));
+  CK(launch_bin(pos, A, nf, S, p.cell[0], p.cell[1], p.cell[2], p.nx, p.ny, slots, recs, offs, nullptr, sc.st));
+  float2 *Bp, *Ap;
+  const size_t plane = (size_t)ny * g->band.Wp;
+  CK(sc.get(&Bp, (size_t)chunk * S * g->npair * plane));
+  CK(sc.get(&Ap, (size_t)chunk * S * plane));
+  const SpreadKernel sk{kSpreadHalf, (float)kSpreadBeta};
+  for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
+    const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
+    const int nfs = nfc * S;
+    CK(launch_splat_row(geo, g->band, recs + (size_t)f0 * A, offs + (size_t)f0 * (S + 1), A, S, nfs, g->npair, sk,
+                        Bp, sc.st));
+    CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
+    TRY_RC(sink(f0, nfc, Ap));
+  }
+  return TACAW_OK;
+}
+
+// Frames per chunk so that `per_frame` bytes of scratch stay under `cap`.
+int64_t chunk_frames(int64_t nf, size_t per_frame, size_t cap) {
+  int64_t c = (int64_t)std::max<size_t>(1, cap / std::max<size_t>(per_frame, 1));
+  return std::min<int64_t>(c, nf);
+}
+
+// Band-limited transmission of nfs slices from Ap (potential column-pass output) or V.
+int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* Ap, const float* V, int nfs,
+                      float2* t, Scratch& sc) {
+  const Geo geo{p.nx, p.ny, ctx->tw};
+  const float sig = (float)sigma_per_VA(p.voltage_ev);
+  const int bl = p.bandlimit_transmission && p.bandlimit > 0.0;
+  if (!bl) {
+    if (Ap) CK(launch_row_pot_out(geo, g->band, Ap, nfs, 2, sig, nullptr, t, sc.st));
+    else CK(launch_row_vt(geo, g->band, V, nfs, 0, sig, t, sc.st));
+    return TACAW_OK;
+  }
+  float2 *Bt, *At;
+  const size_t plane = (size_t)p.ny * g->band.Wp;
+  CK(sc.get(&Bt, (size_t)nfs * plane));
+  CK(sc.get(&At, (size_t)nfs * plane));
+  if (Ap) CK(launch_row_pot_out(geo, g->band, Ap, nfs, 1, sig, nullptr, Bt, sc.st));
+  else CK(launch_row_vt(geo, g->band, V, nfs, 1, sig, Bt, sc.st));
+  CK(launch_col_t(geo, g->band, Bt, nfs, 1.0f / ((float)p.nx * (float)p.ny), At, sc.st));
+  CK(launch_row_tout(geo, g->band, At, nfs, t, sc.st));
+  // Bt/At are released with the scratch at the end of the call
+  return TACAW_OK;
+}
+
+// Initial waves psi0[P][ny][nx] for a convergent probe.
+int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, Scratch& sc, float2** psi0) {
+  const int nx = p.nx, ny = p.ny, P = pr.n_probes;
+  const double Lx = p.cell[0], Ly = p.cell[1];
+  const double kmax = pr.alpha_mrad * 1e-3 / wavelength_A(p.voltage_ev);
+  int W, Wp, mb;
+  std::vector<int> nb;
+  make_band(nx, ny, Lx, Ly, kmax, W, Wp, mb, nb);
+  if (W == 0) return set_err(ctx, TACAW_EINVAL, "probe aperture holds no k point");
+  int64_t count = 0;
+  for (int c = 0; c < W; ++c) count += nb[c] < 0 ? 0 : (nb[c] >= ny / 2 ? ny : 2 * nb[c] + 1);
+  std::vector<float2> ex((size_t)P * Wp, make_float2(0.f, 0.f)), ey((size_t)P * ny);
+  for (int ip = 0; ip < P; ++ip) {
+    const double xp = pr.xy ? pr.xy[2 * ip] : 0.0, yp = pr.xy ? pr.xy[2 * ip + 1] : 0.0;
+    for (int c = 0; c < W; ++c) {
+      const int x = c <= mb ? c : nx - (W - c);
+      const double a = -2.0 * M_PI * kfreq(x, nx, Lx) * xp;
+      ex[(size_t)ip * Wp + c] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    for (int y = 0; y < ny; ++y) {
+      const double a = -2.0 * M_PI * kfreq(y, ny, Ly) * yp;
+      ey[(size_t)ip * ny + y] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  }
+  int* d_nb;
+  float2 *d_ex, *d_ey, *Bpr;
+  CK(sc.get(&d_nb, Wp));
+  CK(sc.get(&d_ex, ex.size()));
+  CK(sc.get(&d_ey, ey.size()));
+  CK(sc.get(&Bpr, (size_t)P * ny * Wp));
+  CK(sc.get(psi0, (size_t)P * ny * nx));
+  CK(cudaMemcpyAsync(d_nb, nb.data(), sizeof(int) * Wp, cudaMemcpyHostToDevice, sc.st));
+  CK(cudaMemcpyAsync(d_ex, ex.data(), sizeof(float2) * ex.size(), cudaMemcpyHostToDevice, sc.st));
+  CK(cudaMemcpyAsync(d_ey, ey.data(), sizeof(float2) * ey.size(), cudaMemcpyHostToDevice, sc.st));
+  const Band ap{W, Wp, mb, d_nb};
+  const Geo geo{nx, ny, ctx->tw};
+  CK(launch_probe_col(geo, ap, d_ex, d_ey, P, (float)(1.0 / std::sqrt((double)count)), Bpr, sc.st));
+  CK(launch_probe_row(geo, ap, Bpr, P, (float)(1.0 / std::sqrt((double)nx * ny)), *psi0, sc.st));
+  CK(cudaStreamSynchronize(sc.st));  // host tables are local
+  return TACAW_OK;
+}
+
+// Multislice of nfc frames whose transmission functions are t[fl][s][ny][nx]; exit waves go to
+// psi_k[p][f0 + fl] of a [P][F_total][ny][nx] stack (zeroed by the caller).
+int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, int nfc, int P, const float2* psi0,
+           int64_t F_total, int64_t f0, float2* psi_k, Scratch& sc, float2* Apsi, float2* Bpsi) {
+  const Geo geo{p.nx, p.ny, ctx->tw};
+  const int S = p.n_slices;
+  const float nq = (float)p.nx * (float)p.ny;
+  const float plane_amp = (float)(1.0 / std::sqrt((double)p.nx * p.ny));
+  for (int s = 0; s < S; ++s) {
+    const bool last = s == S - 1;
+    CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi,
+                        sc.st));
+    CK(launch_slice_col(geo, g->band, last, Bpsi, g->px, g->py,
+                        last ? (float)(1.0 / std::sqrt((double)p.nx * p.ny)) : 1.0f / nq, P, nfc, F_total, f0, Apsi,
+                        psi_k, sc.st));
+  }
+  return TACAW_OK;
+}
+
+int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
+                  int32_t reduce, const int32_t* qsel, int64_t nsel, float* S_out, Scratch& sc);
+
+}  // namespace tacaw
+
+extern "C" {
+
+int tacaw_bin_slices(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, int64_t n_atoms, int64_t nf,
+                     int32_t* slice_out, void* stream) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  TRY_RC(check_params(ctx, params));
+  if (n_atoms < 0 || nf < 1) return set_err(ctx, TACAW_EINVAL, "n_atoms >= 0 and nf >= 1 required");
+  if (n_atoms == 0) return TACAW_OK;
+  if (!is_device_ptr(pos) || !is_device_ptr(slice_out)) return set_err(ctx, TACAW_EINVAL, "pos, slice_out must be device pointers");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc(st);
+  int* offs;
+  CK(sc.get(&offs, (size_t)nf * (params->n_slices + 1)));
+  CK(launch_bin(pos, n_atoms, nf, params->n_slices, params->cell[0], params->cell[1], params->cell[2], params->nx,
+                params->ny, nullptr, nullptr, offs, slice_out, st));
+  return TACAW_OK;
+}
+
+int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z,
+                          int64_t n_atoms, int64_t nf, float* V_out, void* stream) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  TRY_RC(check_params(ctx, params));
+  const tacaw_params& p = *params;
+  if (n_atoms < 0 || nf < 1) return set_err(ctx, TACAW_EINVAL, "n_atoms >= 0 and nf >= 1 required");
+  if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
+  if ((n_atoms > 0 && (!is_device_ptr(pos) || !is_device_ptr(Z))) || !is_device_ptr(V_out))
+    return set_err(ctx, TACAW_EINVAL, "pos, Z and V_out must be device pointers");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  GeoCache* g;
+  TRY_RC(get_geo(ctx, p, &g));
+  Scratch sc(st);
+  int8_t* slots;
+  TRY_RC(make_slots(ctx, Z, n_atoms, true, sc, &slots));
+  const Geo geo{p.nx, p.ny, ctx->tw};
+  const size_t plane = (size_t)p.ny * g->band.Wp;
+  const int64_t chunk = chunk_frames(nf, p.n_slices * plane * 8 * (g->npair + 1), (size_t)1 << 30);
+  return potential_chunks(ctx, p, g, pos, slots, n_atoms, nf, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
+    CK(launch_row_pot_out(geo, g->band, Ap, nfc * p.n_slices, 0, 0.f,
+                          V_out + (size_t)f0 * p.n_slices * p.ny * p.nx, nullptr, st));
+    return TACAW_OK;
+  });
+}
+
+int tacaw_transmission(tacaw_ctx* ctx, const tacaw_params* params, const float* V, int64_t nf, float* t_out,
+                       void* stream) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  TRY_RC(check_params(ctx, params));
+  if (nf < 1) return set_err(ctx, TACAW_EINVAL, "nf >= 1 required");
+  if (!is_device_ptr(V) || !is_device_ptr(t_out)) return set_err(ctx, TACAW_EINVAL, "V, t_out must be device pointers");
+  CK(cudaSetDevice(ctx->device));
+  GeoCache* g;
+  TRY_RC(get_geo(ctx, *params, &g));
+  Scratch sc((cudaStream_t)stream);
+  const int64_t nfs = nf * params->n_slices;
+  const int64_t step = 4096;
+  for (int64_t i = 0; i < nfs; i += step) {
+    const int n = (int)std::min(step, nfs - i);
+    const size_t off = (size_t)i * params->ny * params->nx;
+    TRY_RC(transmission_from(ctx, *params, g, nullptr, V + off, n, reinterpret_cast<float2*>(t_out) + off, sc));
+  }
+  return TACAW_OK;
+}
+
+int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, int64_t nf, const tacaw_probe* probe,
+                    float* psi_k_out, void* stream) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  TRY_RC(check_params(ctx, params));
+  const tacaw_params& p = *params;
+  tacaw_probe pr = probe ? *probe : tacaw_probe{0.0, 1, 0, nullptr};
+  if (nf < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "nf >= 1 and n_probes >= 1 required");
+  if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  if (!is_device_ptr(V) || !is_device_ptr(psi_k_out)) return set_err(ctx, TACAW_EINVAL, "V, psi_k_out must be device pointers");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  GeoCache* g;
+  TRY_RC(get_geo(ctx, p, &g));
+  Scratch sc(st);
+  const int P = pr.n_probes, S = p.n_slices;
+  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
+  float2* psi_k = reinterpret_cast<float2*>(psi_k_out);
+  CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * nq * P * nf, st));
+  float2* psi0 = nullptr;
+  if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
+  const size_t per_frame = (size_t)S * nq * 8 + (size_t)P * plane * 16;
+  const int64_t chunk = chunk_frames(nf, per_frame, (size_t)2 << 30);
+  float2 *t, *Apsi, *Bpsi;
+  CK(sc.get(&t, (size_t)chunk * S * nq));
+  CK(sc.get(&Apsi, (size_t)chunk * P * plane));
+  CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
+  for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
+    const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
+    TRY_RC(transmission_from(ctx, p, g, nullptr, V + (size_t)f0 * S * nq, nfc * S, t, sc));
+    TRY_RC(slices(ctx, p, g, t, nfc, P, psi0, nf, f0, psi_k, sc, Apsi, Bpsi));
+  }
+  return TACAW_OK;
+}
+
+int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
+                   int32_t reduce, const int32_t* q_sel, int64_t n_sel, float* S_out, void* stream) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (P < 1 || F < 1 || nq < 1) return set_err(ctx, TACAW_EINVAL, "P, F, nq must be >= 1");
+  if (!is_device_ptr(psi_k) || !is_device_ptr(S_out) || (q_sel && !is_device_ptr(q_sel)))
+    return set_err(ctx, TACAW_EINVAL, "psi_k, S_out (and q_sel) must be device pointers");
+  if (q_sel && (n_sel < 1 || n_sel > nq)) return set_err(ctx, TACAW_EINVAL, "n_sel must be in [1, nq]");
+  CK(cudaSetDevice(ctx->device));
+  Scratch sc((cudaStream_t)stream);
+  return spectrum_impl(ctx, reinterpret_cast<const float2*>(psi_k), P, F, nq, precision, reduce, q_sel,
+                       q_sel ? n_sel : nq, S_out, sc);
+}
+
+int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z, int64_t n_atoms,
+              int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
+              void* stream) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  TRY_RC(check_params(ctx, params));
+  const tacaw_params& p = *params;
+  tacaw_probe pr = probe ? *probe : tacaw_probe{0.0, 1, 0, nullptr};
+  if (n_atoms < 0 || n_frames < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "bad sizes");
+  if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
+  if (!pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
+  if (!S_out || (!Z && n_atoms > 0)) return set_err(ctx, TACAW_EINVAL, "Z, S_out must not be NULL");
+  if (reduce != TACAW_REDUCE_NONE && reduce != TACAW_REDUCE_DETECTOR) return set_err(ctx, TACAW_EINVAL, "bad reduce");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  GeoCache* g;
+  TRY_RC(get_geo(ctx, p, &g));
+  Scratch sc(st);
+  const int P = pr.n_probes, S = p.n_slices;
+  const int64_t F = n_frames, A = n_atoms;
+  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
+  // inputs
+  const bool pos_dev = A > 0 && is_device_ptr(pos), z_dev = A > 0 && is_device_ptr(Z);
+  const float* d_pos = pos;
+  if (A > 0 && !pos_dev) {
+    float* tmp;
+    CK(sc.get(&tmp, (size_t)F * A * 3));
+    CK(cudaMemcpyAsync(tmp, pos, sizeof(float) * F * A * 3, cudaMemcpyHostToDevice, st));
+    d_pos = tmp;
+  }
+  int8_t* slots;
+  TRY_RC(make_slots(ctx, Z, A, z_dev, sc, &slots));
+  const bool out_dev = is_device_ptr(S_out);
+  const size_t out_elems = reduce == TACAW_REDUCE_NONE ? (size_t)P * F * nq : (size_t)P * F;
+  float* d_S = S_out;
+  if (!out_dev) CK(sc.get(&d_S, out_elems));
+  float2* psi0 = nullptr;
+  if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
+  // exit-wave stack
+  float2* psi_k;
+  CK(sc.get(&psi_k, (size_t)P * F * nq));
+  CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
+  const size_t per_frame = (size_t)S * nq * 8 + (size_t)S * plane * 8 * (g->npair + 3) + (size_t)P * plane * 16;
+  const int64_t chunk = chunk_frames(F, per_frame, (size_t)2 << 30);
+  float2 *t, *Apsi, *Bpsi;
+  CK(sc.get(&t, (size_t)chunk * S * nq));
+  CK(sc.get(&Apsi, (size_t)chunk * P * plane));
+  CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
+  TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
+    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * S, t, sc));
+    return slices(ctx, p, g, t, nfc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi);
+  }));
+  TRY_RC(spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc));
+  if (!out_dev) {
+    CK(cudaMemcpyAsync(S_out, d_S, sizeof(float) * out_elems, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else if (!pos_dev && A > 0) {
+    CK(cudaStreamSynchronize(st));  // the caller's host positions were read asynchronously
+  }
+  return TACAW_OK;
+}
+
+}  // extern "C"
+
+namespace tacaw {
+
+int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
+                  int32_t reduce, const int32_t* qsel, int64_t nsel, float* S_out, Scratch& sc) {
+  if (reduce != TACAW_REDUCE_NONE && reduce != TACAW_REDUCE_DETECTOR) return set_err(ctx, TACAW_EINVAL, "bad reduce");
+  if (precision < TACAW_DFT_FP32 || precision > TACAW_DFT_TF32) return set_err(ctx, TACAW_EINVAL, "bad precision");
+  cudaStream_t st = sc.st;
+  double2* mean;
+  CK(sc.get(&mean, (size_t)P * nsel));
+  CK(launch_mean_f64(psi_k, P, F, nq, qsel, nsel, mean, st));
+  float* S = S_out;
+  if (reduce == TACAW_REDUCE_DETECTOR) CK(sc.get(&S, (size_t)P * F * nq));
+  if (reduce == TACAW_REDUCE_NONE && qsel && nsel < nq) CK(cudaMemsetAsync(S, 0, sizeof(float) * P * F * nq, st));
+  if (precision == TACAW_DFT_FP32) {
+    float2* r;
+    CK(sc.get(&r, (size_t)P * F * nsel));
+    CK(launch_residual_f32(psi_k, mean, P, F, nq, qsel, nsel, r, st));
+    float2* twF;
+    TRY_RC(get_time_tw(ctx, F, &twF));
+    CK(launch_dft_fp32(r, twF, P, F, nsel, nq, qsel, S, st));
+  } else {
+    TRY_RC(spectrum_tc(ctx, psi_k, mean, P, F, nq, precision, qsel, nsel, S, sc));
+  }
+  if (reduce == TACAW_REDUCE_DETECTOR) CK(launch_detector_reduce(S, P, F, nq, qsel, nsel, S_out, st));
+  return TACAW_OK;
+}
+
+}  // namespace tacaw

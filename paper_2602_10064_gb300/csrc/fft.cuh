@@ -1,0 +1,237 @@
+// Device FFT engine for the slice kernels.
+//
+// Every 2D transform of the hot path (potential, transmission band limit, the slice step of
+// the multislice chain in Methods "Multislice Propagation") is split into 1D transforms along
+// rows (x, contiguous) and columns (y, strided).  This header holds the 1D engine: a
+// Stockham autosort FFT whose radix-R butterflies run in registers and whose data exchange
+// between passes goes through shared memory.
+//
+// Thread ownership: a transform of length N is done by T = N / E threads; thread t owns the
+// E elements at positions t + T*e (e = 0..E-1) on entry and on exit, so global loads and
+// stores of a row are coalesced (consecutive t, consecutive addresses).  A pass of radix R
+// (R divides E) runs E/R butterflies per thread; the last pass lands in the owner's own
+// registers, so an N = R1*R2*R3 transform makes two shared-memory exchanges.
+//
+// Twiddles come from a table tw_N[j] = exp(-2 pi i j / N) built on the host in FP64 and
+// rounded to float; the inverse uses the conjugate.  Transforms are unnormalised.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tacaw {
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// a * (SIGN i): forward (SIGN = -1) multiplies by -i, inverse by +i.
+template <int SIGN>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  return SIGN < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// exp(SIGN 2 pi i j / 16) for the small j a radix-16 butterfly needs (j compile-time after unrolling).
+template <int SIGN>
+__device__ __forceinline__ float2 w16(int j) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, r2 = 0.70710678118654752f;
+  float c, s;
+  switch (j & 15) {
+    case 0: c = 1.f; s = 0.f; break;
+    case 1: c = c1; s = s1; break;
+    case 2: c = r2; s = r2; break;
+    case 3: c = s1; s = c1; break;
+    case 4: c = 0.f; s = 1.f; break;
+    case 5: c = -s1; s = c1; break;
+    case 6: c = -r2; s = r2; break;
+    case 7: c = -c1; s = s1; break;
+    case 8: c = -1.f; s = 0.f; break;
+    case 9: c = -c1; s = -s1; break;
+    case 10: c = -r2; s = -r2; break;
+    case 11: c = -s1; s = -c1; break;
+    case 12: c = 0.f; s = -1.f; break;
+    case 13: c = s1; s = -c1; break;
+    case 14: c = r2; s = -r2; break;
+    default: c = c1; s = -s1; break;
+  }
+  return make_float2(c, SIGN < 0 ? -s : s);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft2(float2* u) {
+  float2 a = u[0], b = u[1];
+  u[0] = a + b;
+  u[1] = a - b;
+}
+
+// X[k] = sum_n u[n] exp(SIGN 2 pi i n k / 4), natural order.
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02 = a0 + a2, d02 = a0 - a2, s13 = a1 + a3, d13 = mul_si<SIGN>(a1 - a3);
+  a0 = s02 + s13;
+  a2 = s02 - s13;
+  a1 = d02 + d13;
+  a3 = d02 - d13;
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2* u) {
+  dft4<SIGN>(u[0], u[1], u[2], u[3]);
+}
+
+// Radix-8 as two radix-4 transforms of the even and odd samples.
+template <int SIGN>
+__device__ __forceinline__ void dft8(float2* u) {
+  float2 e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
+  float2 o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
+  dft4<SIGN>(e0, e1, e2, e3);
+  dft4<SIGN>(o0, o1, o2, o3);
+  const float r2 = 0.70710678118654752f;
+  // w8^k = exp(SIGN 2 pi i k / 8)
+  float2 t1 = cmul(o1, make_float2(r2, SIGN * r2));
+  float2 t2 = mul_si<SIGN>(o2);
+  float2 t3 = cmul(o3, make_float2(-r2, SIGN * r2));
+  u[0] = e0 + o0;
+  u[4] = e0 - o0;
+  u[1] = e1 + t1;
+  u[5] = e1 - t1;
+  u[2] = e2 + t2;
+  u[6] = e2 - t2;
+  u[3] = e3 + t3;
+  u[7] = e3 - t3;
+}
+
+// Radix-16 as 4 x 4: inner radix-4 over n1 (stride 4), twiddle w16^(n2 k1), outer radix-4 over n2.
+template <int SIGN>
+__device__ __forceinline__ void dft16(float2* u) {
+  float2 y[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    y[n2][0] = u[n2];
+    y[n2][1] = u[4 + n2];
+    y[n2][2] = u[8 + n2];
+    y[n2][3] = u[12 + n2];
+    dft4<SIGN>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w16<SIGN>(n2 * k1));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1], a3 = y[3][k1];
+    dft4<SIGN>(a0, a1, a2, a3);
+    u[k1] = a0;
+    u[k1 + 4] = a1;
+    u[k1 + 8] = a2;
+    u[k1 + 12] = a3;
+  }
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_r(float2* u) {
+  if constexpr (R == 2) dft2<SIGN>(u);
+  else if constexpr (R == 4) dft4<SIGN>(u);
+  else if constexpr (R == 8) dft8<SIGN>(u);
+  else dft16<SIGN>(u);
+}
+
+// Elements per thread for a transform of length N.
+template <int N>
+struct FftPlan {
+  static constexpr int E = (N <= 64) ? 8 : 16;
+  static constexpr int T = N / E;
+};
+
+// Shared-memory index of position x for one row-owned transform: one pad slot per 16 keeps
+// the stride-R writes of the first pass free of bank conflicts.
+struct RowIdx {
+  int base;
+  __device__ __forceinline__ int operator()(int x) const { return base + x + (x >> 4); }
+};
+template <int N>
+__host__ __device__ constexpr int row_smem_stride() { return N + N / 16; }
+
+// Column-owned transforms: C columns interleaved, column c fastest.
+template <int C>
+struct ColIdx {
+  int c;
+  __device__ __forceinline__ int operator()(int x) const { return x * C + c; }
+};
+
+// One Stockham pass of radix R; NS = product of earlier radices.
+template <int N, int R, int NS, int SIGN, bool LAST, class Idx>
+__device__ __forceinline__ void fft_pass(float2 (&v)[FftPlan<N>::E], float2* sm, const Idx& idx, int t,
+                                         const float2* __restrict__ tw) {
+  constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T, B = E / R;
+  if (!LAST) __syncthreads();  // earlier readers of sm are done
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int bi = t + T * b;
+    const int k = bi & (NS - 1);
+    float2 u[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) u[i] = v[b + B * i];
+    if (NS > 1) {
+#pragma unroll
+      for (int i = 1; i < R; ++i) {
+        float2 w = __ldg(&tw[i * k * (N / (NS * R))]);
+        if (SIGN > 0) w.y = -w.y;
+        u[i] = cmul(u[i], w);
+      }
+    }
+    dft_r<R, SIGN>(u);
+    if (LAST) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[b + B * i] = u[i];
+    } else {
+      const int d = (bi - k) * R + k;
+#pragma unroll
+      for (int i = 0; i < R; ++i) sm[idx(d + i * NS)] = u[i];
+    }
+  }
+  if (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = sm[idx(t + T * e)];
+  }
+}
+
+// Unnormalised length-N transform of the elements owned by this thread (positions t + T e),
+// SIGN = -1 forward, +1 inverse.  All threads of the block must call it together.
+// tw points at the table for length N.
+template <int N, int SIGN, class Idx>
+__device__ __forceinline__ void fft(float2 (&v)[FftPlan<N>::E], float2* sm, const Idx& idx, int t,
+                                    const float2* __restrict__ tw) {
+  if constexpr (N == 32) {
+    fft_pass<32, 8, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<32, 4, 8, SIGN, true>(v, sm, idx, t, tw);
+  } else if constexpr (N == 64) {
+    fft_pass<64, 8, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<64, 8, 8, SIGN, true>(v, sm, idx, t, tw);
+  } else if constexpr (N == 128) {
+    fft_pass<128, 16, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<128, 8, 16, SIGN, true>(v, sm, idx, t, tw);
+  } else if constexpr (N == 256) {
+    fft_pass<256, 16, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<256, 16, 16, SIGN, true>(v, sm, idx, t, tw);
+  } else if constexpr (N == 512) {
+    fft_pass<512, 16, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<512, 16, 16, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<512, 2, 256, SIGN, true>(v, sm, idx, t, tw);
+  } else if constexpr (N == 1024) {
+    fft_pass<1024, 16, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<1024, 16, 16, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<1024, 4, 256, SIGN, true>(v, sm, idx, t, tw);
+  } else if constexpr (N == 2048) {
+    fft_pass<2048, 16, 1, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<2048, 16, 16, SIGN, false>(v, sm, idx, t, tw);
+    fft_pass<2048, 8, 256, SIGN, true>(v, sm, idx, t, tw);
+  } else {
+    static_assert(N == 32, "unsupported FFT length");
+  }
+}
+
+}  // namespace tacaw

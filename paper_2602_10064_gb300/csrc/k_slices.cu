@@ -1,0 +1,737 @@
+// Slice kernels: binning, projected potential, transmission, probe and the multislice step.
+//
+// Every 2D transform is a row pass (FFT along x inside one CTA per G rows) followed by a column
+// pass (FFT along y inside one CTA per C columns); pointwise work is fused into the passes:
+//   potential  (Methods, "Atomic Scattering Potentials"):
+//     spread atoms -> FFT_x | FFT_y, * C M (f_A - i f_B)/Phi, IFFT_y | IFFT_x, Re -> V
+//   transmission (Methods, "Multislice Propagation", t = exp(i sigma V)):
+//     exp(i sigma V) -> FFT_x | FFT_y, * M / Nq, IFFT_y | IFFT_x -> t
+//   slice step  (same section, psi <- IDFT(P M DFT(t psi))):
+//     [IFFT_x] * t, FFT_x | FFT_y, * P M / Nq, IFFT_y    (the IFFT_x of slice s is fused into
+//     the row pass of slice s+1; the last column pass writes psi(k) without the inverse)
+// Between the passes only the in-band columns (|kx| <= kbl) are kept, in compact order.
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "tacaw_internal.cuh"
+
+namespace tacaw {
+
+template <int N>
+struct RowCfg {
+  static constexpr int T = FftPlan<N>::T;
+  static constexpr int G = (256 / T) > 32 ? 32 : (256 / T);
+  static constexpr int THREADS = G * T;
+  static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
+};
+
+template <int N>
+struct ColCfg {
+  static constexpr int T = FftPlan<N>::T;
+  static constexpr int C = (256 / T) > 32 ? 32 : ((256 / T) < 4 ? 4 : 256 / T);
+  static constexpr int THREADS = C * T;
+  static constexpr int SMEM = N * C * (int)sizeof(float2);
+};
+
+// Batch index over (grid.y, grid.z); batches beyond nb return before any barrier.
+__device__ __forceinline__ int batch_index() { return blockIdx.y + gridDim.y * blockIdx.z; }
+static dim3 batch_grid(int gx, int64_t nb) {
+  unsigned y = (unsigned)(nb < 65535 ? nb : 65535);
+  unsigned z = (unsigned)((nb + y - 1) / y);
+  return dim3((unsigned)gx, y, z);
+}
+
+template <int N>
+__device__ __forceinline__ void load_row_compact(float2 (&v)[FftPlan<N>::E], const float2* __restrict__ src,
+                                                 const Band& b, int t) {
+  constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int c = band_x_col(b, N, t + T * e);
+    v[e] = c >= 0 ? src[c] : make_float2(0.f, 0.f);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_row_compact(const float2 (&v)[FftPlan<N>::E], float2* __restrict__ dst,
+                                                  const Band& b, int t) {
+  constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int c = band_x_col(b, N, t + T * e);
+    if (c >= 0) dst[c] = v[e];
+  }
+}
+
+// ============================================================================================
+// a1: slice binning.  One CTA per frame; stable scatter, so every slice list keeps atom order.
+// ============================================================================================
+constexpr int BIN_THREADS = 1024;
+constexpr int BIN_MAX_S = 256;
+
+__device__ __forceinline__ int slice_of(double z, double Lz, int S) {
+  const double dz = Lz / (double)S;
+  const double zw = __dsub_rn(z, __dmul_rn(Lz, floor(z / Lz)));
+  int s = (int)floor(zw / dz);
+  if (s >= S) s = S - 1;
+  if (s < 0) s = 0;
+  return s;
+}
+
+__device__ __forceinline__ void grid_coord(double x, double L, int n, int& i0, float& fr) {
+  const double xw = __dsub_rn(x, __dmul_rn(L, floor(x / L)));
+  const double u = __dmul_rn(xw, (double)n / L);
+  double fl = floor(u);
+  int i = (int)fl;
+  double f = __dsub_rn(u, fl);
+  if (i >= n) { i -= n; }
+  if (i < 0) { i += n; }
+  i0 = i;
+  fr = (float)f;
+}
+
+__global__ void __launch_bounds__(BIN_THREADS) k_bin(const float* __restrict__ pos, int A, int S, double Lx,
+                                                      double Ly, double Lz, int nx, int ny,
+                                                      const int8_t* __restrict__ slot_of_atom,
+                                                      AtomRec* __restrict__ recs, int* __restrict__ offs,
+                                                      int* __restrict__ slice_out) {
+  __shared__ int counts[BIN_MAX_S];
+  __shared__ int cursor[BIN_MAX_S];
+  __shared__ int wcount[BIN_THREADS / 32][BIN_MAX_S];
+  const int f = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float* P = pos + (size_t)f * A * 3;
+  for (int s = tid; s < S; s += BIN_THREADS) counts[s] = 0;
+  __syncthreads();
+  for (int j = tid; j < A; j += BIN_THREADS) {
+    const int s = slice_of((double)P[3 * j + 2], Lz, S);
+    atomicAdd(&counts[s], 1);
+    if (slice_out) slice_out[(size_t)f * A + j] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int s = 0; s < S; ++s) {
+      offs[(size_t)f * (S + 1) + s] = run;
+      cursor[s] = run;
+      run += counts[s];
+    }
+    offs[(size_t)f * (S + 1) + S] = run;
+  }
+  if (!recs) return;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = 0; base < A; base += BIN_THREADS) {
+    for (int i = tid; i < (BIN_THREADS / 32) * S; i += BIN_THREADS) wcount[i / S][i % S] = 0;
+    __syncthreads();
+    const int j = base + tid;
+    const bool valid = j < A;
+    const int s = valid ? slice_of((double)P[3 * j + 2], Lz, S) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) wcount[w][s] = __popc(peers);
+    __syncthreads();
+    for (int ss = tid; ss < S; ss += BIN_THREADS) {
+      int run = cursor[ss];
+      for (int ww = 0; ww < BIN_THREADS / 32; ++ww) {
+        const int c = wcount[ww][ss];
+        wcount[ww][ss] = run;
+        run += c;
+      }
+      cursor[ss] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const int p = wcount[w][s] + rank;
+      AtomRec r;
+      int ix, iy;
+      grid_coord((double)P[3 * j], Lx, nx, ix, r.fx);
+      grid_coord((double)P[3 * j + 1], Ly, ny, iy, r.fy);
+      r.ixy = ix | (iy << 16);
+      r.jslot = j | ((int)slot_of_atom[j] << 24);
+      recs[(size_t)f * A + p] = r;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
+                       int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
+                       cudaStream_t st) {
+  if (S > BIN_MAX_S || nf <= 0) return cudaErrorInvalidValue;
+  k_bin<<<(unsigned)nf, BIN_THREADS, 0, st>>>(pos, (int)A, S, Lx, Ly, Lz, nx, ny, slot_of_atom, recs, offs,
+                                             slice_out);
+  return cudaGetLastError();
+}
+
+// ============================================================================================
+// a2: potential.  Row pass: spread the atoms of one slice and one species pair onto G rows
+// (gather per grid point, candidates in atom order, so the sum is deterministic), then FFT_x.
+// ============================================================================================
+__device__ __forceinline__ float es_kernel(float z, float beta) {
+  const float a = 1.f - z * z;
+  return a > 0.f ? expf(beta * (sqrtf(a) - 1.f)) : 0.f;
+}
+
+constexpr int SPREAD_MAX_W = 16;
+
+template <int NX>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+    k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
+                int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
+  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  // candidate tables alias the FFT scratch (used strictly before the transform)
+  float* phx = reinterpret_cast<float*>(smraw);       // [NT][SPREAD_MAX_W]
+  float* phy = phx + NT * SPREAD_MAX_W;                // [NT][G]
+  int* cx0 = reinterpret_cast<int*>(phy + NT * G);     // [NT] first column of the footprint
+  int* cim = cx0 + NT;                                 // [NT] 1: imaginary part (odd slot)
+  __shared__ int wtot[NW];
+
+  const int bidx = batch_index();
+  if (bidx >= nbatch) return;
+  const int pair = bidx % npair, fs = bidx / npair, f = fs / S, s = fs % S;
+  const int tid = threadIdx.x, g = tid / T, t = tid % T, lane = tid & 31, w = tid >> 5;
+  const int ny = geo.ny, y0 = blockIdx.x * G;
+  const int h = sk.half, W2 = 2 * h;
+  const int lo = offs[(size_t)f * (S + 1) + s], hi = offs[(size_t)f * (S + 1) + s + 1];
+  const AtomRec* R = recs + (size_t)f * A;
+
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+
+  for (int base = lo; base < hi; base += NT) {
+    const int j = base + tid;
+    bool cand = false;
+    AtomRec r;
+    if (j < hi) {
+      r = R[j];
+      const int slot = r.jslot >> 24;
+      if ((slot >> 1) == pair) {
+        const int iy0 = r.ixy >> 16;
+        const int rr = (iy0 + 1 - h - y0 + 2 * ny) & (ny - 1);
+        cand = (rr < G) || (rr + W2 - 1 >= ny);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) wtot[w] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {
+      const int c = wtot[ww];
+      before += (ww < w) ? c : 0;
+      total += c;
+    }
+    if (cand) {
+      const int ci = before + __popc(bal & ((1u << lane) - 1u));
+      const int ix0 = r.ixy & 0xffff, iy0 = r.ixy >> 16;
+      cx0[ci] = (ix0 + 1 - h + geo.nx) & (geo.nx - 1);
+      cim[ci] = (r.jslot >> 24) & 1;
+      for (int d = 0; d < W2; ++d) phx[ci * SPREAD_MAX_W + d] = es_kernel(((float)(d + 1 - h) - r.fx) / (float)h, sk.beta);
+      for (int gg = 0; gg < G; ++gg) {
+        int d = (y0 + gg - iy0 + ny) & (ny - 1);
+        if (d > ny / 2) d -= ny;
+        phy[ci * G + gg] = (d >= 1 - h && d <= h) ? es_kernel(((float)d - r.fy) / (float)h, sk.beta) : 0.f;
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < total; ++c) {
+      const float wy = phy[c * G + g];
+      if (wy == 0.f) continue;
+      const int x0 = cx0[c];
+      const bool im = cim[c] != 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int dx = (t + T * e - x0 + geo.nx) & (geo.nx - 1);
+        if (dx < W2) {
+          const float a = wy * phx[c * SPREAD_MAX_W + dx];
+          if (im) v[e].y += a;
+          else v[e].x += a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  fft<NX, -1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  store_row_compact<NX>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
+}
+
+// Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+    k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
+              float2* __restrict__ Ap) {
+  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int fs = batch_index();
+  if (fs >= nbatch) return;
+  const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
+  const ColIdx<C> idx{c};
+  const float2* tw = geo.tw + NY;
+  float2 acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = make_float2(0.f, 0.f);
+  for (int pr = 0; pr < npair; ++pr) {
+    const float2* src = Bp + (size_t)(fs * npair + pr) * NY * b.Wp + cc;
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+    fft<NY, -1>(v, sm, idx, t, tw);
+    const float2* m = mtab + (size_t)pr * NY * b.Wp + cc;
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
+  }
+  fft<NY, +1>(acc, sm, idx, t, tw);
+  float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
+#pragma unroll
+  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = acc[e];
+}
+
+// Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
+// t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
+template <int NX>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+    k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
+                  float* __restrict__ V, float2* __restrict__ out) {
+  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int fs = batch_index();
+  if (fs >= nbatch) return;
+  const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
+  const RowIdx idx{g * row_smem_stride<NX>()};
+  float2 v[E];
+  load_row_compact<NX>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
+  fft<NX, +1>(v, sm, idx, t, geo.tw + NX);
+  const size_t row = ((size_t)fs * ny + y) * NX;
+  if (mode == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) V[row + t + T * e] = v[e].x;
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    float sn, cs;
+    sincosf(sigma * v[e].x, &sn, &cs);
+    v[e] = make_float2(cs, sn);
+  }
+  if (mode == 2) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
+    return;
+  }
+  fft<NX, -1>(v, sm, idx, t, geo.tw + NX);
+  store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
+}
+
+// ============================================================================================
+// a3: transmission from a stored V.
+// ============================================================================================
+template <int NX>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+    k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
+             float2* __restrict__ out) {
+  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int fs = batch_index();
+  if (fs >= nbatch) return;
+  const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
+  const size_t row = ((size_t)fs * ny + y) * NX;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    float sn, cs;
+    sincosf(sigma * V[row + t + T * e], &sn, &cs);
+    v[e] = make_float2(cs, sn);
+  }
+  if (!bandlimit) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
+    return;
+  }
+  fft<NX, -1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
+}
+
+// Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+    k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
+  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int fs = batch_index();
+  if (fs >= nbatch) return;
+  const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
+  const ColIdx<C> idx{c};
+  const float2* tw = geo.tw + NY;
+  const float2* src = Bt + (size_t)fs * NY * b.Wp + cc;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+  fft<NY, -1>(v, sm, idx, t, tw);
+  const int nb = cc < b.W ? b.colnb[cc] : -1;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int n = fftfreq_index(t + T * e, NY);
+    v[e] = (abs(n) <= nb) ? scale * v[e] : make_float2(0.f, 0.f);
+  }
+  fft<NY, +1>(v, sm, idx, t, tw);
+  float2* dst = At + (size_t)fs * NY * b.Wp + cc;
+#pragma unroll
+  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
+}
+
+// Row pass out of the band limit: IFFT_x -> t (full row).
+template <int NX>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+    k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
+  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int fs = batch_index();
+  if (fs >= nbatch) return;
+  const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
+  float2 v[E];
+  load_row_compact<NX>(v, At + ((size_t)fs * ny + y) * b.Wp, b, t);
+  fft<NX, +1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  float2* dst = tout + ((size_t)fs * ny + y) * NX;
+#pragma unroll
+  for (int e = 0; e < E; ++e) dst[t + T * e] = v[e];
+}
+
+// ============================================================================================
+// Probe: psi0(k) = A(k) exp(-2 pi i k.r_p) amp, then a unitary inverse transform.
+// ============================================================================================
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+    k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey, int P, float amp,
+                float2* __restrict__ Bpr) {
+  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int p = batch_index();
+  if (p >= P) return;
+  const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
+  const int nb = cc < ap.W ? ap.colnb[cc] : -1;
+  const float2 exv = cc < ap.W ? ex[(size_t)p * ap.Wp + cc] : make_float2(0.f, 0.f);
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int row = t + T * e, n = fftfreq_index(row, NY);
+    v[e] = (abs(n) <= nb) ? amp * cmul(exv, ey[(size_t)p * NY + row]) : make_float2(0.f, 0.f);
+  }
+  fft<NY, +1>(v, sm, ColIdx<C>{c}, t, geo.tw + NY);
+  float2* dst = Bpr + (size_t)p * NY * ap.Wp + cc;
+#pragma unroll
+  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * ap.Wp] = v[e];
+}
+
+template <int NX>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+    k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
+  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int p = batch_index();
+  if (p >= P) return;
+  const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
+  float2 v[E];
+  load_row_compact<NX>(v, Bpr + ((size_t)p * ny + y) * ap.Wp, ap, t);
+  fft<NX, +1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  float2* dst = psi0 + ((size_t)p * ny + y) * NX;
+#pragma unroll
+  for (int e = 0; e < E; ++e) dst[t + T * e] = scale * v[e];
+}
+
+// ============================================================================================
+// a4/a5: the slice step.
+// ============================================================================================
+template <int NX, bool FIRST, bool PLANE>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+    k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
+                const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
+                float2* __restrict__ Bpsi) {
+  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int w = batch_index();
+  if (w >= nwaves) return;
+  const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
+  const int p = w / nfc, fl = w - p * nfc;
+  const RowIdx idx{g * row_smem_stride<NX>()};
+  float2 v[E];
+  if (FIRST) {
+    if (PLANE) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = make_float2(plane_amp, 0.f);
+    } else {
+      const float2* src = psi0 + ((size_t)p * ny + y) * NX;
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = src[t + T * e];
+    }
+  } else {
+    load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
+    fft<NX, +1>(v, sm, idx, t, geo.tw + NX);
+  }
+  const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = cmul(v[e], trow[t + T * e]);
+  fft<NX, -1>(v, sm, idx, t, geo.tw + NX);
+  store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
+}
+
+template <int NY, bool LAST>
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+    k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
+                const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
+                float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
+  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int w = batch_index();
+  if (w >= nwaves) return;
+  const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
+  const ColIdx<C> idx{c};
+  const float2* tw = geo.tw + NY;
+  const float2* src = Bpsi + (size_t)w * NY * b.Wp + cc;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+  fft<NY, -1>(v, sm, idx, t, tw);
+  const int nb = cc < b.W ? b.colnb[cc] : -1;
+  const float2 pxc = cc < b.W ? px[cc] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int row = t + T * e, n = fftfreq_index(row, NY);
+    v[e] = (abs(n) <= nb) ? scale * cmul(cmul(v[e], pxc), py[row]) : make_float2(0.f, 0.f);
+  }
+  if (LAST) {
+    if (cc < b.W) {
+      const int p = w / nfc, fl = w - p * nfc;
+      const int x = band_col_x(b, geo.nx, cc);
+      float2* dst = psi_k + (((size_t)p * F_total + f0 + fl) * NY) * geo.nx + x;
+#pragma unroll
+      for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * geo.nx] = v[e];
+    }
+    return;
+  }
+  fft<NY, +1>(v, sm, idx, t, tw);
+  float2* dst = Apsi + (size_t)w * NY * b.Wp + cc;
+#pragma unroll
+  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
+}
+
+// ============================================================================================
+// Potential multiplier table (FP64 evaluation, float storage).
+// ============================================================================================
+__device__ double form_factor_f64(const double* c, double q) {
+  const double q2 = q * q;
+  double f = 0.0;
+  for (int i = 0; i < 3; ++i) f += c[2 * i] / (q2 + c[2 * i + 1]);
+  for (int i = 0; i < 3; ++i) f += c[6 + 2 * i] * exp(-c[7 + 2 * i] * q2);
+  return f;
+}
+
+__global__ void k_build_mtab(int nx, int ny, Band b, int npair, int nslot, const double* __restrict__ coef,
+                             const double* __restrict__ phix, const double* __restrict__ phiy, double Lx, double Ly,
+                             double pref, float2* __restrict__ mtab) {
+  const int64_t total = (int64_t)npair * ny * b.Wp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int cc = (int)(i % b.Wp);
+    const int row = (int)((i / b.Wp) % ny);
+    const int pr = (int)(i / ((int64_t)b.Wp * ny));
+    float2 out = make_float2(0.f, 0.f);
+    const int n = fftfreq_index(row, ny);
+    if (cc < b.W && abs(n) <= b.colnb[cc]) {
+      const int m = fftfreq_index(band_col_x(b, nx, cc), nx);
+      const double kx = (double)m / Lx, ky = (double)n / Ly;
+      const double q = sqrt(kx * kx + ky * ky);
+      const double fa = form_factor_f64(coef + 12 * (2 * pr), q);
+      const double fb = (2 * pr + 1 < nslot) ? form_factor_f64(coef + 12 * (2 * pr + 1), q) : 0.0;
+      const double sc = pref / (phix[cc] * phiy[row]);
+      out = make_float2((float)(sc * fa), (float)(-sc * fb));
+    }
+    mtab[i] = out;
+  }
+}
+
+// ============================================================================================
+// launchers
+// ============================================================================================
+template <class K>
+static cudaError_t prep(K kernel, int smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaSuccess;
+}
+
+#define TACAW_DISPATCH(N, FN, ...)     \
+  switch (N) {                         \
+    case 32: return FN<32>(__VA_ARGS__);   \
+    case 64: return FN<64>(__VA_ARGS__);   \
+    case 128: return FN<128>(__VA_ARGS__); \
+    case 256: return FN<256>(__VA_ARGS__); \
+    case 512: return FN<512>(__VA_ARGS__); \
+    case 1024: return FN<1024>(__VA_ARGS__); \
+    default: return cudaErrorInvalidValue; \
+  }
+
+template <int NX>
+static int splat_smem() {
+  const int tables = RowCfg<NX>::THREADS * (SPREAD_MAX_W + RowCfg<NX>::G + 2) * 4;
+  return tables > RowCfg<NX>::SMEM ? tables : RowCfg<NX>::SMEM;
+}
+
+template <int NX>
+static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A,
+                               int S, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
+  if (2 * sk.half > SPREAD_MAX_W) return cudaErrorInvalidValue;
+  const int smem = splat_smem<NX>();
+  cudaError_t e = prep(k_splat_row<NX>, smem);
+  if (e != cudaSuccess) return e;
+  const int nb = nfs * npair;
+  k_splat_row<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nb), RowCfg<NX>::THREADS, smem, st>>>(
+      g, b, recs, offs, (int)A, S, npair, nb, sk, Bp);
+  return cudaGetLastError();
+}
+cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A, int S,
+                             int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, offs, A, S, nfs, npair, sk, Bp, st);
+}
+
+template <int NY>
+static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
+                             float2* Ap, cudaStream_t st) {
+  k_col_pot<NY><<<batch_grid(b.Wp / ColCfg<NY>::C, nfs), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(
+      g, b, Bp, mtab, npair, nfs, Ap);
+  return cudaGetLastError();
+}
+cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
+                           float2* Ap, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, col_pot_n, g, b, Bp, mtab, npair, nfs, Ap, st);
+}
+
+template <int NX>
+static cudaError_t row_pot_out_n(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
+                                 float* V, float2* out, cudaStream_t st) {
+  k_row_pot_out<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nfs), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(
+      g, b, Ap, nfs, mode, sigma, V, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
+                               float* V, float2* out, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, row_pot_out_n, g, b, Ap, nfs, mode, sigma, V, out, st);
+}
+
+template <int NX>
+static cudaError_t row_vt_n(const Geo& g, const Band& b, const float* V, int nfs, int bl, float sigma, float2* out,
+                            cudaStream_t st) {
+  k_row_vt<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nfs), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(
+      g, b, V, nfs, bl, sigma, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, int bandlimit, float sigma,
+                          float2* out, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, row_vt_n, g, b, V, nfs, bandlimit, sigma, out, st);
+}
+
+template <int NY>
+static cudaError_t col_t_n(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
+                           cudaStream_t st) {
+  k_col_t<NY><<<batch_grid(b.Wp / ColCfg<NY>::C, nfs), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(g, b, Bt, nfs,
+                                                                                                   scale, At);
+  return cudaGetLastError();
+}
+cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
+                         cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, col_t_n, g, b, Bt, nfs, scale, At, st);
+}
+
+template <int NX>
+static cudaError_t row_tout_n(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st) {
+  k_row_tout<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nfs), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(g, b, At,
+                                                                                                      nfs, t);
+  return cudaGetLastError();
+}
+cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, row_tout_n, g, b, At, nfs, t, st);
+}
+
+template <int NY>
+static cudaError_t probe_col_n(const Geo& g, const Band& ap, const float2* ex, const float2* ey, int P, float amp,
+                               float2* Bpr, cudaStream_t st) {
+  k_probe_col<NY><<<batch_grid(ap.Wp / ColCfg<NY>::C, P), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(
+      g, ap, ex, ey, P, amp, Bpr);
+  return cudaGetLastError();
+}
+cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, int P, float amp,
+                             float2* Bpr, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, probe_col_n, g, ap, ex, ey, P, amp, Bpr, st);
+}
+
+template <int NX>
+static cudaError_t probe_row_n(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
+                               cudaStream_t st) {
+  k_probe_row<NX><<<batch_grid(g.ny / RowCfg<NX>::G, P), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(g, ap, Bpr, P,
+                                                                                                     scale, psi0);
+  return cudaGetLastError();
+}
+cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
+                             cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, probe_row_n, g, ap, Bpr, P, scale, psi0, st);
+}
+
+template <int NX>
+static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane, const float2* Apsi,
+                               const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
+                               float2* Bpsi, cudaStream_t st) {
+  const int nw = P * nfc;
+  const dim3 grid = batch_grid(g.ny / RowCfg<NX>::G, nw);
+  constexpr int TH = RowCfg<NX>::THREADS, SM = RowCfg<NX>::SMEM;
+  if (first && plane)
+    k_slice_row<NX, true, true><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);
+  else if (first)
+    k_slice_row<NX, true, false><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);
+  else
+    k_slice_row<NX, false, false><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);
+  return cudaGetLastError();
+}
+cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, const float2* Apsi,
+                             const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
+                             float2* Bpsi, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, slice_row_n, g, b, first, plane, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi, st);
+}
+
+template <int NY>
+static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
+                               const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
+                               float2* Apsi, float2* psi_k, cudaStream_t st) {
+  const int nw = P * nfc;
+  const dim3 grid = batch_grid(b.Wp / ColCfg<NY>::C, nw);
+  constexpr int TH = ColCfg<NY>::THREADS, SM = ColCfg<NY>::SMEM;
+  if (last)
+    k_slice_col<NY, true><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, Apsi, psi_k);
+  else
+    k_slice_col<NY, false><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, Apsi, psi_k);
+  return cudaGetLastError();
+}
+cudaError_t launch_slice_col(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
+                             const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
+                             float2* Apsi, float2* psi_k, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, slice_col_n, g, b, last, Bpsi, px, py, scale, P, nfc, F_total, f0, Apsi, psi_k, st);
+}
+
+cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot, const double* coef_slots,
+                              const double* phix, const double* phiy, double Lx, double Ly, double pref,
+                              float2* mtab, cudaStream_t st) {
+  const int64_t total = (int64_t)npair * g.ny * b.Wp;
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  k_build_mtab<<<blocks, 256, 0, st>>>(g.nx, g.ny, b, npair, nslot, coef_slots, phix, phiy, Lx, Ly, pref, mtab);
+  return cudaGetLastError();
+}
+
+}  // namespace tacaw

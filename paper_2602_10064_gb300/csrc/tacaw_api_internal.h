@@ -1,0 +1,82 @@
+// Host-side internals shared by the translation units of libtacaw.so: the context, its
+// caches, stream-ordered scratch and the error helpers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tacaw.h"
+#include "tacaw_internal.cuh"
+
+namespace tacaw {
+struct Serving;
+}
+
+struct GeoCache {
+  using Band = tacaw::Band;
+  Band band{}, aperture{};
+  int* colnb = nullptr;
+  float2* px = nullptr;   // [Wp] propagator along x for compact columns
+  float2* py = nullptr;   // [ny]
+  float2* mtab = nullptr; // [npair][ny][Wp]
+  double* phix = nullptr;
+  double* phiy = nullptr;
+  double* coef_slots = nullptr;
+  int32_t* qsel = nullptr;  // in-band q indices, ascending
+  int64_t nsel = 0;
+  int npair = 0, nslot = 0;
+  uint64_t ff_version = 0;
+};
+
+struct tacaw_ctx {
+  int device = 0;
+  uint64_t budget = 0;
+  std::string err;
+  std::recursive_mutex mu;
+  float2* tw = nullptr;  // FFT twiddles: length-N table at tw + N (N = 2 .. 2048)
+  std::vector<int32_t> ffZ;
+  std::vector<double> ffcoef;
+  int32_t* d_ffZ = nullptr;
+  uint64_t ff_version = 0;
+  std::map<std::vector<double>, std::unique_ptr<GeoCache>> geos;
+  std::map<int64_t, float2*> time_tw;
+  std::vector<void*> owned;
+  tacaw::Serving* serving = nullptr;
+};
+
+
+namespace tacaw {
+
+// Stream-ordered scratch that frees itself on the stream.
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <class T>
+  cudaError_t get(T** p, size_t n) {
+    void* v = nullptr;
+    cudaError_t e = cudaMallocAsync(&v, sizeof(T) * std::max<size_t>(n, 1), st);
+    if (e == cudaSuccess) ptrs.push_back(v);
+    *p = static_cast<T*>(v);
+    return e;
+  }
+};
+
+
+int set_err(tacaw_ctx* c, int code, const char* fmt, ...);
+int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where);
+int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out);
+// tensor-core time transform (k_dft_tc.cu)
+int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, int64_t nq,
+                int32_t precision, const int32_t* qsel, int64_t nsel, float* S, Scratch& sc);
+// serving loop (serving.cpp)
+void serving_shutdown(tacaw_ctx* ctx);
+
+}  // namespace tacaw

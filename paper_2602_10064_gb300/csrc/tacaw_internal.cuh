@@ -1,0 +1,92 @@
+// Internal declarations shared by the CUDA translation units of libtacaw.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace tacaw {
+
+// Columns of an nx-point axis kept after a circular mask, stored compactly in FFT order:
+// compact column c < W holds x = c for c <= mb and x = nx - (W - c) otherwise.  Wp rounds W
+// up to a multiple of 32 (padding columns are zero).  colnb[c] is the largest |n| of the
+// in-band rows of that column (-1 for padding), so (row n, column c) is inside the disc iff
+// |n| <= colnb[c].
+struct Band {
+  int W, Wp, mb;
+  const int* colnb;
+};
+
+// Grid shape plus the FFT twiddle tables (table for length N starts at tw + N).
+struct Geo {
+  int nx, ny;
+  const float2* tw;
+};
+
+// One atom after binning, in the order of its slice list.  ix0/iy0 = floor of the grid
+// coordinate (x wrapped into [0, Lx), times nx / Lx, in FP64), fx/fy the remainder.
+struct AtomRec {
+  float fx, fy;
+  int ixy;    // ix0 | iy0 << 16
+  int jslot;  // atom index | species slot << 24
+};
+
+__device__ __forceinline__ int fftfreq_index(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+__device__ __forceinline__ int band_col_x(const Band& b, int nx, int c) { return c <= b.mb ? c : nx - (b.W - c); }
+__device__ __forceinline__ int band_x_col(const Band& b, int nx, int x) {
+  return x <= b.mb ? x : (x >= nx - b.mb ? x - nx + b.W : -1);
+}
+
+// ---- host launchers (k_slices.cu) ---------------------------------------------------------
+struct SpreadKernel {
+  int half;    // h = w / 2 grid points
+  float beta;  // exp(beta (sqrt(1 - z^2) - 1))
+};
+
+cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
+                       int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
+                       cudaStream_t st);
+cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A, int S,
+                             int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st);
+cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
+                           float2* Ap, cudaStream_t st);
+// mode 0: store V; mode 1: t = exp(i sigma V), band-limit pass input (FFT_x, compact);
+// mode 2: t = exp(i sigma V) stored directly (no transmission band limit).
+cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
+                               float* V, float2* out, cudaStream_t st);
+cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, int bandlimit, float sigma,
+                          float2* out, cudaStream_t st);
+cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
+                         cudaStream_t st);
+cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st);
+cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, int P, float amp,
+                             float2* Bpr, cudaStream_t st);
+cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
+                             cudaStream_t st);
+// One slice s for n_waves = P * nfc waves; wave w = p * nfc + fl uses t[(fl * S + s)].
+cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, const float2* Apsi,
+                             const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
+                             float2* Bpsi, cudaStream_t st);
+// last = 0: Apsi = IFFT_y(P M scale FFT_y(Bpsi)); last = 1: psi_k[p][f0 + fl] = P M scale FFT_y(Bpsi).
+cudaError_t launch_slice_col(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
+                             const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
+                             float2* Apsi, float2* psi_k, cudaStream_t st);
+// mtab[pair][ny][Wp] = C M(k) (f_2p(|k|) - i f_2p+1(|k|)) / (Phi_x Phi_y), FP64 evaluation.
+cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot, const double* coef_slots,
+                              const double* phix, const double* phiy, double Lx, double Ly, double pref,
+                              float2* mtab, cudaStream_t st);
+
+// ---- time transform (k_spectrum.cu) -----------------------------------------------------
+cudaError_t launch_mean_f64(const float2* psi, int64_t P, int64_t F, int64_t nq, const int32_t* qsel,
+                            int64_t nsel, double2* mean, cudaStream_t st);
+// residual r[p][n][j] = psi[p][n][qsel[j]] - mean[p][j] in FP64, rounded to float
+cudaError_t launch_residual_f32(const float2* psi, const double2* mean, int64_t P, int64_t F, int64_t nq,
+                                const int32_t* qsel, int64_t nsel, float2* r, cudaStream_t st);
+// S[p][m][qsel[j]] = |sum_n W[m][n] r[p][n][j]|^2 (FP32), W from the length-F table
+cudaError_t launch_dft_fp32(const float2* r, const float2* twF, int64_t P, int64_t F, int64_t nsel, int64_t nq,
+                            const int32_t* qsel, float* S, cudaStream_t st);
+// SI[p][m] = sum_j S[p][m][qsel[j]] (FP64 accumulation, deterministic)
+cudaError_t launch_detector_reduce(const float* S, int64_t P, int64_t F, int64_t nq, const int32_t* qsel,
+                                   int64_t nsel, float* SI, cudaStream_t st);
+
+}  // namespace tacaw

@@ -1,0 +1,300 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded inputs.
+
+Tolerances: integer work (slice binning) is bit-exact.  Floating point is compared by
+relative L2 norm.  The path runs in FP32 (unit roundoff 6e-8); a 2D FFT of N^2 points adds
+O(log2 N) roundings per element and every slice applies two of them, so intermediate fields
+(V, t, psi) are held to 2e-5 and the spectrum S to the stated 1e-4 in the FP32 path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL_FIELD = 2e-5
+TOL_S = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2602_10064_gb300 as T
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = T.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def small_rocksalt(n_frames=4, grid=64, S=5, seed=31):
+    R, Z, cell = workloads.rocksalt(4.21, (2, 2, 2))
+    rng = workloads.SplitMix64(seed)
+    modes = workloads.random_modes(rng, 4, cell, (2, 2, 2), amp=0.05)
+    return workloads._finish("rs-small", R, Z, cell, modes, n_frames, 5.0, S, grid, 0.5)
+
+
+def rect_diamond(n_frames=4, seed=32):
+    w = workloads.diamond_si(n_frames=n_frames, grid=64, n_slices=4, reps=(2, 1, 1), seed=seed)
+    w.ny = 32  # cell 10.86 x 5.43: rectangular grid
+    return w
+
+
+# ------------------------------------------------------------------------------------------
+# a1 slice binning: bit-exact
+# ------------------------------------------------------------------------------------------
+def test_bin_slices_bit_exact(ctx, T):
+    rng = np.random.default_rng(0)
+    Lz, S = 10.86, 8
+    dz = Lz / S
+    z = np.concatenate([rng.uniform(-2 * Lz, 3 * Lz, 4000), np.arange(-16, 32) * dz, [0.0, Lz, -Lz, 2 * Lz],
+                        np.nextafter(np.float32(np.arange(0, 8) * dz), np.float32(-1e9))]).astype(np.float32)
+    pos = np.zeros((2, z.size, 3), np.float32)
+    pos[0, :, 2] = z
+    pos[1, :, 2] = z[::-1]
+    p = T.make_params(64, 64, S, (10.86, 10.86, Lz))
+    got = ctx.bin_slices(p, dev(pos)).cpu().numpy()
+    want = np.array([[oracle.slice_index(float(v), Lz, S) for v in pos[f, :, 2]] for f in range(2)])
+    assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------------------------------------
+# a2 projected potential
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_off"])
+def test_potential_parity(ctx, T, case):
+    w = {"c1": lambda: workloads.diamond_si(n_frames=2), "rocksalt": small_rocksalt, "rect": rect_diamond,
+         "bl_off": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4)}[case]()
+    kw = {"bandlimit": 0.0} if case == "bl_off" else {}
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p = T.params_of(w, **kw)
+    V = ctx.build_potential(p, dev(w.pos[:2]), dev(w.Z)).cpu().numpy()
+    op = oracle.params_of(w, **kw)
+    for f in range(2):
+        for s in range(w.n_slices):
+            ref = oracle.potential_slice(op, w.pos[f], w.Z, s, w.form_Z, w.form_coef)
+            assert rel(V[f, s], ref) < TOL_FIELD, (f, s, rel(V[f, s], ref))
+
+
+def test_potential_empty_slice_is_zero(ctx, T):
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=4)
+    pos = w.pos.copy()
+    pos[:, :, 2] = 0.1  # every atom in slice 0
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    V = ctx.build_potential(T.params_of(w), dev(pos), dev(w.Z)).cpu().numpy()
+    assert np.abs(V[0, 1:]).max() == 0.0
+    ref = oracle.potential_slice(oracle.params_of(w), pos[0], w.Z, 0, w.form_Z, w.form_coef)
+    assert rel(V[0, 0], ref) < TOL_FIELD
+
+
+def test_unknown_species_is_rejected(ctx, T):
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=2)
+    fz, fc = workloads.placeholder_form_factors([8])
+    ctx.load_form_factors(fz, fc)
+    with pytest.raises(T.TacawError) as ei:
+        ctx.build_potential(T.params_of(w), dev(w.pos), dev(w.Z))
+    assert ei.value.code == T.TACAW_EINVAL
+    ctx.load_form_factors(w.form_Z, w.form_coef)  # still usable
+    ctx.build_potential(T.params_of(w), dev(w.pos), dev(w.Z))
+
+
+def test_bad_grid_is_rejected(ctx, T):
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=2)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    with pytest.raises(T.TacawError):
+        ctx.build_potential(T.params_of(w, nx=100), dev(w.pos), dev(w.Z))
+
+
+# ------------------------------------------------------------------------------------------
+# a3 transmission (from the oracle's V, to isolate the step)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("blt", [1, 0])
+def test_transmission_parity(ctx, T, blt):
+    w = workloads.diamond_si(n_frames=1, grid=64, n_slices=3)
+    op = oracle.params_of(w, bandlimit_transmission=blt)
+    V = np.stack([oracle.potential_slice(op, w.pos[0], w.Z, s, w.form_Z, w.form_coef) for s in range(3)])
+    V32 = V.astype(np.float32)
+    t = ctx.transmission(T.params_of(w, bandlimit_transmission=blt), dev(V32[None])).cpu().numpy()[0]
+    for s in range(3):
+        ref = oracle.transmission(op, V32[s].astype(np.float64))
+        assert rel(t[s], ref) < TOL_FIELD
+
+
+# ------------------------------------------------------------------------------------------
+# a4/a5 multislice
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["plane", "probe", "rocksalt", "rect", "one_slice"])
+def test_propagate_parity(ctx, T, case):
+    if case == "plane":
+        w = workloads.diamond_si(n_frames=2)
+    elif case == "probe":
+        w = workloads.diamond_si(n_frames=2, grid=64, n_slices=6)
+        w.alpha_mrad, w.probes = 30.0, np.array([[0.0, 0.0], [1.37, 4.11], [7.5, 2.2]])
+    elif case == "rocksalt":
+        w = small_rocksalt(n_frames=2)
+    elif case == "rect":
+        w = rect_diamond(n_frames=2)
+    else:
+        w = workloads.diamond_si(n_frames=2, grid=32, n_slices=1)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p = T.params_of(w)
+    V = ctx.build_potential(p, dev(w.pos), dev(w.Z))
+    psi = ctx.propagate(p, V, T.probe_of(w)).cpu().numpy()
+    op = oracle.params_of(w)
+    for f in range(w.n_frames):
+        ref = oracle.multislice_frame(op, w.pos[f], w.Z, w.form_Z, w.form_coef, w.alpha_mrad,
+                                      w.probes if w.alpha_mrad > 0 else None)
+        for ip in range(ref.shape[0]):
+            assert rel(psi[ip, f], ref[ip]) < TOL_FIELD, (f, ip, rel(psi[ip, f], ref[ip]))
+
+
+def test_vacuum_is_exact_fresnel(ctx, T):
+    N, L, Lz, S = 64, 12.0, 21.0, 5
+    p = T.make_params(N, N, S, (L, L, Lz))
+    fz, fc = workloads.placeholder_form_factors([14])
+    ctx.load_form_factors(fz, fc)
+    import torch
+    V = torch.zeros((1, S, N, N), dtype=torch.float32, device="cuda")
+    pr = T.ProbeSpec(40.0, np.array([[1.3, 2.9]]))
+    psi = ctx.propagate(p, V, pr).cpu().numpy()[0, 0]
+    op = oracle.params(N, N, S, (L, L, Lz))
+    psi0 = oracle.fft2(oracle.probe(op, 40.0, 1.3, 2.9), -1) / N
+    k = np.fft.fftfreq(N, d=L / N)
+    k2 = k[:, None] ** 2 + k[None, :] ** 2
+    want = psi0 * oracle.mask(op) * np.exp(-1j * np.pi * oracle.wavelength(100e3) * Lz * k2)
+    assert rel(psi, want) < TOL_FIELD
+
+
+# ------------------------------------------------------------------------------------------
+# a6-a8 time transform
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("P,F,nq", [(1, 64, 128), (2, 96, 300), (3, 17, 70), (1, 1, 5)])
+def test_spectrum_fp32_parity(ctx, T, P, F, nq):
+    psi = workloads.random_exit_waves(P, F, nq, seed=P * F + nq)
+    S = ctx.spectrum(dev(psi)).cpu().numpy()
+    ref = oracle.spectrum(psi)
+    scale = max(np.linalg.norm(ref), 1e-30)
+    assert np.linalg.norm(S - ref) / scale < 1e-5
+
+
+def test_spectrum_qsel_and_detector(ctx, T):
+    import torch
+    P, F, nq = 2, 64, 200
+    psi = workloads.random_exit_waves(P, F, nq, seed=5)
+    qs = np.array(sorted(np.random.default_rng(1).choice(nq, 77, replace=False)), np.int32)
+    S = ctx.spectrum(dev(psi), q_sel=dev(qs)).cpu().numpy()
+    ref = oracle.spectrum(psi)
+    mask = np.zeros(nq, bool)
+    mask[qs] = True
+    assert np.abs(S[:, :, ~mask]).max() == 0.0
+    assert rel(S[:, :, mask], ref[:, :, mask]) < 1e-5
+    SI = ctx.spectrum(dev(psi), reduce=T.REDUCE_DETECTOR, q_sel=dev(qs)).cpu().numpy()
+    assert SI.shape == (P, F)
+    assert rel(SI, ref[:, :, mask].sum(axis=2)) < 1e-5
+
+
+def test_spectrum_mean_subtraction_fp64(ctx, T):
+    # a large elastic part (1e3) over a small signal: only FP64 mean/residual keeps 1e-5
+    psi = workloads.random_exit_waves(1, 128, 64, seed=9, elastic=1e3, inelastic=1e-2)
+    S = ctx.spectrum(dev(psi)).cpu().numpy()
+    ref = oracle.spectrum(psi)
+    assert rel(S, ref) < 1e-5
+
+
+# ------------------------------------------------------------------------------------------
+# the whole path
+# ------------------------------------------------------------------------------------------
+def test_run_config1_within_tolerance(ctx, T):
+    w = workloads.config1()
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
+    ref = oracle.tacaw(w)
+    err = rel(S, ref)
+    print(f"config 1: S rel L2 = {err:.3e}")
+    assert err < TOL_S
+
+
+def test_run_probe_scan(ctx, T):
+    w = workloads.diamond_si(n_frames=8, grid=64, n_slices=6, seed=41)
+    w.alpha_mrad, w.probes = 30.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
+    ref = oracle.tacaw(w)
+    assert rel(S, ref) < TOL_S
+    SI = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w), reduce=T.REDUCE_DETECTOR).cpu().numpy()
+    assert rel(SI, ref.sum(axis=(2, 3))) < TOL_S
+
+
+def test_run_single_mode_peaks(ctx, T):
+    m0, F = 2, 32
+    w = workloads.single_mode_si(n_frames=F, m0=m0)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()[0]
+    per_bin = S.reshape(F, -1).sum(axis=1)
+    best = 1 + int(np.argmax(per_bin[1:]))
+    assert best in (m0, F - m0)
+    assert rel(S, oracle.tacaw(w)[0]) < TOL_S
+
+
+def test_run_static_is_zero(ctx, T):
+    w = workloads.static_si()
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
+    assert np.abs(S).max() == 0.0
+
+
+def test_run_host_buffers_match_device(ctx, T):
+    import torch
+    w = workloads.diamond_si(n_frames=8, grid=32, n_slices=4, seed=43)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p, pr = T.params_of(w), T.probe_of(w)
+    S_dev = ctx.run(p, dev(w.pos), dev(w.Z), pr).cpu().numpy()
+    pos_h = torch.from_numpy(w.pos).pin_memory()
+    Z_h = torch.from_numpy(w.Z)
+    out_h = torch.empty((1, w.n_frames, w.ny, w.nx), dtype=torch.float32).pin_memory()
+    T.tacaw_run(ctx.h, p, pos_h, Z_h, w.n_atoms, w.n_frames, pr, T.DFT_FP32, T.REDUCE_NONE, out_h)
+    assert np.array_equal(out_h.numpy(), S_dev)
+
+
+def test_run_is_deterministic(ctx, T):
+    w = workloads.diamond_si(n_frames=8, grid=64, n_slices=4, seed=44)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    a = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
+    b = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------------------------------
+# full-size configuration 2 (512^2, 8000 atoms, 20 slices): sampled frames
+# ------------------------------------------------------------------------------------------
+def test_config2_sampled_frames(ctx, T):
+    w = workloads.config2(n_frames=16)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p = T.params_of(w)
+    frames = [0, 13]
+    V = ctx.build_potential(p, dev(w.pos[frames]), dev(w.Z))
+    psi = ctx.propagate(p, V, T.probe_of(w)).cpu().numpy()[0]
+    op = oracle.params_of(w)
+    refs = oracle.multislice(op, w.pos[frames], w.Z, w.form_Z, w.form_coef)[0]
+    for i in range(len(frames)):
+        assert rel(psi[i], refs[i]) < TOL_FIELD, rel(psi[i], refs[i])
