@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the TACAW hot path (multislice + time transform) on one node.
+
+One step = the whole hot path for one synthetic trajectory: slice binning, projected
+potential, transmission, multislice for every (probe, frame), FP64 mean/residual, time
+transform and |.|^2, through tacaw_run on device-resident inputs.  The default workload is
+the plane-wave rocksalt trajectory (8000 atoms, 1024 frames at 5 fs, 512^2, 20 slices).
+With N ranks (torchrun) every rank runs its own independently seeded trajectory (weak
+scaling, no collective on the data path); value = all ranks' wave-slice steps / max time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2]
+
+--impl reference times the FP64 CPU oracle (the only reference this method has) on a bounded
+sample of the same workload, on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wave-slice steps/s & S(q,ω) spectra/s vs plain path; p50/p99 latency @tol"
+UNIT = "wave-slice steps/s"
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2, "bf16": 3, "tf32": 4}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload(name, seed_offset=0):
+    import workloads
+    if name == "c1":
+        w = workloads.diamond_si(seed=1 + seed_offset, name="c1-diamond-si-64x128sq")
+    elif name == "c2":
+        w = workloads.config2(seed=2 + seed_offset)
+    elif name == "c3":
+        w = workloads.config3(seed=3 + seed_offset)
+    elif name == "c4":
+        w = workloads.config4(seed=4 + seed_offset)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w
+
+
+def workload_config(w, name, precision):
+    return {"workload": w.name, "config": name, "atoms": int(w.n_atoms), "frames": int(w.n_frames),
+            "grid": [int(w.ny), int(w.nx)], "slices": int(w.n_slices), "probes": int(w.n_probes),
+            "alpha_mrad": float(w.alpha_mrad), "dt_fs": float(w.dt_fs), "voltage_kev": w.voltage_ev / 1e3,
+            "bandlimit": "2/3", "time_transform": precision,
+            "l2": "256 MiB buffer written between timed steps (and each step streams > 3 GB)"}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline helpers
+# ------------------------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "of measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "of fallback"
+
+
+def src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_10064_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """dram bytes per launch from the committed ncu summary, if it matches the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("src") != src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# FP32 lanes per SM (4 SMSPs x 32), SMs: the ALU roofline of the FFT kernels
+FP32_LANES, N_SM = 128, 152
+
+
+def roofline(prof, steps, wname, sm_mhz):
+    name = max(prof, key=lambda k: prof[k][0])
+    ms, nl, by, fl = prof[name]
+    per_launch_s = ms / 1e3 / nl
+    peaks, tag = measured_peaks()
+    gbs = by / nl / per_launch_s / 1e9
+    tfl = fl / nl / per_launch_s / 1e12
+    if name.startswith("dft_") and "fp32" not in name:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        r = {"bound": "tensor", "achieved": tfl, "peak": peak, "unit": "TFLOP/s", "frac": tfl / peak}
+    else:
+        alu_peak = 2.0 * FP32_LANES * N_SM * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+        hbm = peaks["hbm_gbs"]
+        if gbs / hbm >= tfl / alu_peak:
+            r = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+        else:
+            r = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
+                 "peak_basis": "FP32 FMA: 2 x 128 lanes x 152 SMs x 2.07 GHz"}
+        r["hbm_gbs_achieved"] = gbs
+        r["fp32_tflops_achieved"] = tfl
+    r.update({"kernel": name, "launches_per_step": nl / steps, "ms_per_launch": per_launch_s * 1e3,
+              "algorithmic_bytes_per_launch": by / nl, "algorithmic_flops_per_launch": fl / nl,
+              "traffic": ncu_traffic(name, wname), "peak_source": tag})
+    return r
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline (the FP64 oracle as it stands) on a bounded sample
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(w, budget_s=20.0):
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    p = oracle.params_of(w)
+    probes = w.probes if w.alpha_mrad > 0 else None
+    t0 = time.perf_counter()
+    one = oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
+    t1 = time.perf_counter() - t0
+    threads = oracle.num_threads()
+    # frames run in parallel (one per thread): n frames take about ceil(n / threads) * t1
+    n = max(1, min(w.n_frames, threads * max(1, int(budget_s / max(t1, 1e-3)))))
+    t0 = time.perf_counter()
+    psi = oracle.multislice(p, w.pos[:n], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
+    S = oracle.spectrum(psi)
+    dt = time.perf_counter() - t0
+    units = n * w.n_slices * w.n_probes
+    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} of {w.n_frames} frames x {w.n_probes} probe(s) x {w.n_slices} slices, "
+                      f"multislice + time transform of those frames, {dt:.1f} s"}, psi, n
+
+
+# ------------------------------------------------------------------------------------------
+# the reference arm: the oracle on the host cores
+# ------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    import oracle
+    oracle.build()
+    p = oracle.params_of(w)
+    probes = w.probes if w.alpha_mrad > 0 else None
+    per_step = max(1, int(args.ref_frames))
+    for _ in range(args.warmup):
+        oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
+    times = []
+    for k in range(args.steps):
+        fr = w.pos[(k * per_step) % w.n_frames:][:per_step]
+        t0 = time.perf_counter()
+        psi = oracle.multislice(p, fr, w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
+        oracle.spectrum(psi)
+        times.append(time.perf_counter() - t0)
+    units = per_step * w.n_slices * w.n_probes * args.steps
+    tot = sum(times)
+    v = units / tot
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, args.workload, "fp64 oracle"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{per_step} frame(s) per step of {w.n_frames}, multislice + time transform"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-frames", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_2602_10064_gb300 as T
+
+    w = make_workload(args.workload, seed_offset=1000 * rank)
+    prec = PRECISIONS[args.precision]
+    ctx = T.Context(local)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    params, probe = T.params_of(w), T.probe_of(w)
+    pos = torch.from_numpy(w.pos).cuda()
+    Z = torch.from_numpy(w.Z).cuda()
+    P, F = w.n_probes, w.n_frames
+    S = torch.empty((P, F, w.ny, w.nx), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        T.tacaw_run(ctx.h, params, pos, Z, w.n_atoms, F, probe, prec, T.REDUCE_NONE, S, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    T.tacaw_profile_begin(ctx.h)
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between timed steps (not timed)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    prof = T.tacaw_profile_end(ctx.h)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([tot_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    units_rank = P * F * w.n_slices * args.steps
+    value = units_rank * world / tot_s
+    spectra = P * args.steps * world / tot_s
+
+    # end to end through the C ABI with host buffers: H2D of the positions and species,
+    # D2H of S, inside the timed region
+    pos_h = torch.from_numpy(w.pos).pin_memory()
+    Z_h = torch.from_numpy(w.Z)
+    S_h = torch.empty((P, F, w.ny, w.nx), dtype=torch.float32).pin_memory()
+    T.tacaw_run(ctx.h, params, pos_h, Z_h, w.n_atoms, F, probe, prec, T.REDUCE_NONE, S_h, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        T.tacaw_run(ctx.h, params, pos_h, Z_h, w.n_atoms, F, probe, prec, T.REDUCE_NONE, S_h, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": units_rank * world / args.steps * args.e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(w.pos.nbytes + w.Z.nbytes), "d2h_bytes_per_step": int(S_h.numel() * 4),
+           "steps": args.e2e_steps, "api": "tacaw_run with pinned host pos/Z/S"}
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    launches = sum(v[1] for v in prof.values()) / args.steps
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded harmonic-mode trajectory; placeholder Kirkland-form table)",
+        "config": workload_config(w, args.workload, args.precision),
+        "spectra_per_s": spectra, "px_slices_per_s": value * w.nx * w.ny,
+        "step_ms": step_ms,
+        "roofline": roofline(prof, args.steps, w.name, clk.get("sm_mhz")),
+        "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                        "gbs": v[2] / max(v[0], 1e-9) / 1e6, "tflops": v[3] / max(v[0], 1e-9) / 1e9}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "gpu_launches": int(round(launches)),
+        "clocks": clk, "e2e": e2e,
+    }
+    ctx_sample = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb, psi_ref, n = cpu_baseline(w, args.cpu_seconds)
+        out["cpu_baseline"] = cb
+        # the same frames on the GPU: exit-wave agreement at full size
+        V = ctx.build_potential(params, pos[:n].contiguous(), Z)
+        psi = ctx.propagate(params, V, probe).cpu().numpy()
+        err = float(np.linalg.norm(psi - psi_ref) / np.linalg.norm(psi_ref))
+        out["tol"] = {"psi_rel_l2_vs_oracle": err, "frames": n,
+                      "S_rel_l2_bound": "1e-4 (tests/test_gpu_parity.py at oracle sizes)"}
+    ctx.close()
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -110,7 +110,9 @@ int tacaw_bin_slices(tacaw_ctx* ctx, const tacaw_params* params, const float* po
  * The structure factor is evaluated by spreading each atom onto the grid with an
  * exponential-of-semicircle kernel (width 12, beta 24) and deconvolving after the FFT.
  * pos: DEVICE float32 [nf][n_atoms][3] (A); Z: DEVICE int32 [n_atoms] (each Z must be in the
- * loaded table); V_out: DEVICE float32 [nf][S][ny][nx] (V*A). */
+ * loaded table); V_out: DEVICE float32 [nf][S][ny][nx] (V*A).  The spread structure factor is
+ * accurate only inside a band limit of at most 2/3 of Nyquist; EINVAL for bandlimit <= 0 or
+ * > 2/3 (the same holds for tacaw_run). */
 int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z,
                           int64_t n_atoms, int64_t nf, float* V_out, void* stream);
 
@@ -144,6 +146,16 @@ int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int
 int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z, int64_t n_atoms,
               int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
               void* stream);
+
+/* Diagnostics.  tacaw_profile_begin starts recording a CUDA event pair around every kernel
+ * launch of the calls that follow, on the stream each launch uses.  tacaw_profile_end stops,
+ * waits for the recorded events and reports per kernel class i < max_n (in first-launch order):
+ * its name (NUL-terminated, at most 31 characters, at names + 32 i), total milliseconds,
+ * launch count, and the algorithmic bytes and flops those launches account for.  *n_out
+ * receives the number of classes.  Any output pointer may be NULL. */
+int tacaw_profile_begin(tacaw_ctx* ctx);
+int tacaw_profile_end(tacaw_ctx* ctx, char* names, double* ms, int64_t* launches, double* bytes, double* flops,
+                      int32_t max_n, int32_t* n_out);
 
 #ifdef __cplusplus
 }

@@ -108,6 +108,8 @@ def lib():
             "tacaw_propagate": (C.c_int, [vp, pp, vp, i64, prp, vp, vp]),
             "tacaw_spectrum": (C.c_int, [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp, vp]),
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
+            "tacaw_profile_begin": (C.c_int, [vp]),
+            "tacaw_profile_end": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -119,7 +121,7 @@ def lib():
 def exported_symbols():
     return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
-            "tacaw_spectrum", "tacaw_run"]
+            "tacaw_spectrum", "tacaw_run", "tacaw_profile_begin", "tacaw_profile_end"]
 
 
 def _ptr(x):
@@ -205,6 +207,26 @@ def tacaw_spectrum(ctx, psi_k, P, F, nq, precision, reduce, q_sel, n_sel, S_out,
 def tacaw_run(ctx, params, pos, Z, n_atoms, n_frames, probe: ProbeSpec, precision, reduce, S_out, stream=None):
     return _check(ctx, lib().tacaw_run(ctx, C.byref(params), _ptr(pos), _ptr(Z), n_atoms, n_frames,
                                        C.byref(probe.c), precision, reduce, _ptr(S_out), _stream(stream)))
+
+
+def tacaw_profile_begin(ctx):
+    return _check(ctx, lib().tacaw_profile_begin(ctx))
+
+
+def tacaw_profile_end(ctx, max_n=64):
+    """Per-kernel-class totals since tacaw_profile_begin: {name: (ms, launches, bytes, flops)}."""
+    names = C.create_string_buffer(32 * max_n)
+    ms = (C.c_double * max_n)()
+    nl = (C.c_int64 * max_n)()
+    by = (C.c_double * max_n)()
+    fl = (C.c_double * max_n)()
+    n = C.c_int32()
+    _check(ctx, lib().tacaw_profile_end(ctx, names, ms, nl, by, fl, max_n, C.byref(n)))
+    out = {}
+    for i in range(min(n.value, max_n)):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+        out[nm] = (ms[i], nl[i], by[i], fl[i])
+    return out
 
 
 # ------------------------------------------------------------------------------------------

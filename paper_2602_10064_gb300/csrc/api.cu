@@ -116,6 +116,32 @@ int set_err(tacaw_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+static cudaEvent_t prof_event(tacaw_ctx* c) {
+  Profiler& P = c->prof;
+  if (P.next == P.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    P.pool.push_back(e);
+  }
+  return P.pool[P.next++];
+}
+
+ProfScope::ProfScope(tacaw_ctx* c, const char* name, cudaStream_t s, double bytes, double flops) : ctx(c), st(s) {
+  if (!c->prof.on) return;
+  rec.name = name;
+  rec.bytes = bytes;
+  rec.flops = flops;
+  rec.a = prof_event(c);
+  rec.b = prof_event(c);
+  if (!rec.a || !rec.b) return;
+  active = cudaEventRecord(rec.a, st) == cudaSuccess;
+}
+
+ProfScope::~ProfScope() {
+  if (!active) return;
+  if (cudaEventRecord(rec.b, st) == cudaSuccess) ctx->prof.recs.push_back(rec);
+}
+
 int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return TACAW_OK;
   if (e == cudaErrorMemoryAllocation) return set_err(c, TACAW_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
@@ -156,6 +182,18 @@ int is_device_ptr(const void* p) {
     return 0;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The spreading potential resolves the modes |k| <= kbl from the N-point grid, which needs
+// the aliases at N - kbl to stay outside the band: kbl <= (2/3) Nyquist (1.5x headroom).
+constexpr double kMaxSpreadBandlimit = 2.0 / 3.0 + 1e-12;
+
+int check_spread_band(tacaw_ctx* ctx, const tacaw_params* p) {
+  if (!(p->bandlimit > 0.0) || p->bandlimit > kMaxSpreadBandlimit)
+    return set_err(ctx, TACAW_EINVAL,
+                   "building the potential needs a band limit in (0, 2/3] of Nyquist (got %g): the spread "
+                   "structure factor is accurate only inside it", p->bandlimit);
+  return TACAW_OK;
 }
 
 int check_params(tacaw_ctx* ctx, const tacaw_params* p) {
@@ -422,7 +460,10 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
   int* offs;
   CK(sc.get(&recs, (size_t)nf * std::max<int64_t>(A, 1)));
   CK(sc.get(&offs, (size_t)nf * (S + 1)));
-  CK(launch_bin(pos, A, nf, S, p.cell[0], p.cell[1], p.cell[2], p.nx, p.ny, slots, recs, offs, nullptr, sc.st));
+  {
+    ProfScope ps(ctx, "bin", sc.st, (double)nf * A * 28, 0);
+    CK(launch_bin(pos, A, nf, S, p.cell[0], p.cell[1], p.cell[2], p.nx, p.ny, slots, recs, offs, nullptr, sc.st));
+  }
   float2 *Bp, *Ap;
   const size_t plane = (size_t)ny * g->band.Wp;
   CK(sc.get(&Bp, (size_t)chunk * S * g->npair * plane));
@@ -431,9 +472,19 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
   for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
     const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
     const int nfs = nfc * S;
-    CK(launch_splat_row(geo, g->band, recs + (size_t)f0 * A, offs + (size_t)f0 * (S + 1), A, S, nfs, g->npair, sk,
-                        Bp, sc.st));
-    CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
+    const double W8 = (double)g->band.W * 8.0, fx = 5.0 * p.nx * std::log2((double)p.nx),
+                 fy = 5.0 * ny * std::log2((double)ny);
+    {
+      ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 + (double)nfs * g->npair * ny * W8,
+                   (double)nfs * g->npair * ny * fx);
+      CK(launch_splat_row(geo, g->band, recs + (size_t)f0 * A, offs + (size_t)f0 * (S + 1), A, S, nfs, g->npair,
+                          sk, Bp, sc.st));
+    }
+    {
+      ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
+                   (double)nfs * (g->npair + 1) * g->band.W * fy);
+      CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
+    }
     TRY_RC(sink(f0, nfc, Ap));
   }
   return TACAW_OK;
@@ -451,19 +502,37 @@ int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const 
   const Geo geo{p.nx, p.ny, ctx->tw};
   const float sig = (float)sigma_per_VA(p.voltage_ev);
   const int bl = p.bandlimit_transmission && p.bandlimit > 0.0;
+  const double W8 = (double)g->band.W * 8.0, row = (double)nfs * p.ny, fx = 5.0 * p.nx * std::log2((double)p.nx),
+               fy = 5.0 * p.ny * std::log2((double)p.ny);
   if (!bl) {
-    if (Ap) CK(launch_row_pot_out(geo, g->band, Ap, nfs, 2, sig, nullptr, t, sc.st));
-    else CK(launch_row_vt(geo, g->band, V, nfs, 0, sig, t, sc.st));
+    if (Ap) {
+      ProfScope ps(ctx, "row_pot_t", sc.st, row * (W8 + 8.0 * p.nx), row * fx);
+      CK(launch_row_pot_out(geo, g->band, Ap, nfs, 2, sig, nullptr, t, sc.st));
+    } else {
+      ProfScope ps(ctx, "row_vt", sc.st, row * 12.0 * p.nx, 0);
+      CK(launch_row_vt(geo, g->band, V, nfs, 0, sig, t, sc.st));
+    }
     return TACAW_OK;
   }
   float2 *Bt, *At;
   const size_t plane = (size_t)p.ny * g->band.Wp;
   CK(sc.get(&Bt, (size_t)nfs * plane));
   CK(sc.get(&At, (size_t)nfs * plane));
-  if (Ap) CK(launch_row_pot_out(geo, g->band, Ap, nfs, 1, sig, nullptr, Bt, sc.st));
-  else CK(launch_row_vt(geo, g->band, V, nfs, 1, sig, Bt, sc.st));
-  CK(launch_col_t(geo, g->band, Bt, nfs, 1.0f / ((float)p.nx * (float)p.ny), At, sc.st));
-  CK(launch_row_tout(geo, g->band, At, nfs, t, sc.st));
+  if (Ap) {
+    ProfScope ps(ctx, "row_pot_t", sc.st, row * 2 * W8, row * 2 * fx);
+    CK(launch_row_pot_out(geo, g->band, Ap, nfs, 1, sig, nullptr, Bt, sc.st));
+  } else {
+    ProfScope ps(ctx, "row_vt", sc.st, row * (4.0 * p.nx + W8), row * fx);
+    CK(launch_row_vt(geo, g->band, V, nfs, 1, sig, Bt, sc.st));
+  }
+  {
+    ProfScope ps(ctx, "col_t", sc.st, 2.0 * nfs * p.ny * W8, 2.0 * nfs * g->band.W * fy);
+    CK(launch_col_t(geo, g->band, Bt, nfs, 1.0f / ((float)p.nx * (float)p.ny), At, sc.st));
+  }
+  {
+    ProfScope ps(ctx, "row_tout", sc.st, row * (W8 + 8.0 * p.nx), row * fx);
+    CK(launch_row_tout(geo, g->band, At, nfs, t, sc.st));
+  }
   // Bt/At are released with the scratch at the end of the call
   return TACAW_OK;
 }
@@ -520,11 +589,20 @@ int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, 
   const float plane_amp = (float)(1.0 / std::sqrt((double)p.nx * p.ny));
   for (int s = 0; s < S; ++s) {
     const bool last = s == S - 1;
-    CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi,
-                        sc.st));
-    CK(launch_slice_col(geo, g->band, last, Bpsi, g->px, g->py,
-                        last ? (float)(1.0 / std::sqrt((double)p.nx * p.ny)) : 1.0f / nq, P, nfc, F_total, f0, Apsi,
-                        psi_k, sc.st));
+    const double W8 = (double)g->band.W * 8.0, rows = (double)P * nfc * p.ny,
+                 fx = 5.0 * p.nx * std::log2((double)p.nx), fy = 5.0 * p.ny * std::log2((double)p.ny);
+    {
+      const double in = s > 0 ? W8 : (psi0 ? 8.0 * p.nx : 0.0);
+      ProfScope ps(ctx, "slice_row", sc.st, rows * (in + 8.0 * p.nx + W8), rows * (s > 0 ? 2 : 1) * fx);
+      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi,
+                          sc.st));
+    }
+    {
+      ProfScope ps(ctx, "slice_col", sc.st, rows * 2 * W8, (double)P * nfc * g->band.W * (last ? 1 : 2) * fy);
+      CK(launch_slice_col(geo, g->band, last, Bpsi, g->px, g->py,
+                          last ? (float)(1.0 / std::sqrt((double)p.nx * p.ny)) : 1.0f / nq, P, nfc, F_total, f0,
+                          Apsi, psi_k, sc.st));
+    }
   }
   return TACAW_OK;
 }
@@ -561,6 +639,7 @@ int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const floa
   TRY_RC(check_params(ctx, params));
   const tacaw_params& p = *params;
   if (n_atoms < 0 || nf < 1) return set_err(ctx, TACAW_EINVAL, "n_atoms >= 0 and nf >= 1 required");
+  TRY_RC(check_spread_band(ctx, params));
   if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
   if ((n_atoms > 0 && (!is_device_ptr(pos) || !is_device_ptr(Z))) || !is_device_ptr(V_out))
     return set_err(ctx, TACAW_EINVAL, "pos, Z and V_out must be device pointers");
@@ -661,6 +740,7 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   tacaw_probe pr = probe ? *probe : tacaw_probe{0.0, 1, 0, nullptr};
   if (n_atoms < 0 || n_frames < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "bad sizes");
   if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  TRY_RC(check_spread_band(ctx, params));
   if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
   if (!pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
   if (!S_out || (!Z && n_atoms > 0)) return set_err(ctx, TACAW_EINVAL, "Z, S_out must not be NULL");
@@ -714,6 +794,51 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   return TACAW_OK;
 }
 
+int tacaw_profile_begin(tacaw_ctx* ctx) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->prof.recs.clear();
+  ctx->prof.next = 0;
+  ctx->prof.on = true;
+  return TACAW_OK;
+}
+
+int tacaw_profile_end(tacaw_ctx* ctx, char* names, double* ms, int64_t* launches, double* bytes, double* flops,
+                      int32_t max_n, int32_t* n_out) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->prof.on = false;
+  std::vector<std::string> order;
+  std::map<std::string, std::tuple<double, int64_t, double, double>> acc;
+  for (const ProfRec& r : ctx->prof.recs) {
+    CK(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    if (!acc.count(r.name)) order.push_back(r.name);
+    auto& a = acc[r.name];
+    std::get<0>(a) += t;
+    std::get<1>(a) += 1;
+    std::get<2>(a) += r.bytes;
+    std::get<3>(a) += r.flops;
+  }
+  ctx->prof.recs.clear();
+  ctx->prof.next = 0;
+  const int n = (int)order.size();
+  if (n_out) *n_out = n;
+  for (int i = 0; i < n && i < max_n; ++i) {
+    const auto& a = acc[order[i]];
+    if (names) {
+      std::strncpy(names + 32 * i, order[i].c_str(), 31);
+      names[32 * i + 31] = 0;
+    }
+    if (ms) ms[i] = std::get<0>(a);
+    if (launches) launches[i] = std::get<1>(a);
+    if (bytes) bytes[i] = std::get<2>(a);
+    if (flops) flops[i] = std::get<3>(a);
+  }
+  return TACAW_OK;
+}
+
 }  // extern "C"
 
 namespace tacaw {
@@ -725,21 +850,32 @@ int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, int
   cudaStream_t st = sc.st;
   double2* mean;
   CK(sc.get(&mean, (size_t)P * nsel));
-  CK(launch_mean_f64(psi_k, P, F, nq, qsel, nsel, mean, st));
+  const double pfq = (double)P * F * nsel;
+  {
+    ProfScope ps(ctx, "mean_f64", st, pfq * 8 + (double)P * nsel * 16, pfq * 2);
+    CK(launch_mean_f64(psi_k, P, F, nq, qsel, nsel, mean, st));
+  }
   float* S = S_out;
   if (reduce == TACAW_REDUCE_DETECTOR) CK(sc.get(&S, (size_t)P * F * nq));
   if (reduce == TACAW_REDUCE_NONE && qsel && nsel < nq) CK(cudaMemsetAsync(S, 0, sizeof(float) * P * F * nq, st));
   if (precision == TACAW_DFT_FP32) {
     float2* r;
     CK(sc.get(&r, (size_t)P * F * nsel));
-    CK(launch_residual_f32(psi_k, mean, P, F, nq, qsel, nsel, r, st));
+    {
+      ProfScope ps(ctx, "residual_f32", st, pfq * 16, pfq * 2);
+      CK(launch_residual_f32(psi_k, mean, P, F, nq, qsel, nsel, r, st));
+    }
     float2* twF;
     TRY_RC(get_time_tw(ctx, F, &twF));
+    ProfScope ps(ctx, "dft_fp32", st, pfq * 12, pfq * 8.0 * F);
     CK(launch_dft_fp32(r, twF, P, F, nsel, nq, qsel, S, st));
   } else {
     TRY_RC(spectrum_tc(ctx, psi_k, mean, P, F, nq, precision, qsel, nsel, S, sc));
   }
-  if (reduce == TACAW_REDUCE_DETECTOR) CK(launch_detector_reduce(S, P, F, nq, qsel, nsel, S_out, st));
+  if (reduce == TACAW_REDUCE_DETECTOR) {
+    ProfScope ps(ctx, "detector_reduce", st, pfq * 4, pfq);
+    CK(launch_detector_reduce(S, P, F, nq, qsel, nsel, S_out, st));
+  }
   return TACAW_OK;
 }
 

@@ -32,7 +32,21 @@ struct GeoCache {
   uint64_t ff_version = 0;
 };
 
+// Per-kernel CUDA-event timing (diagnostics; off unless tacaw_profile_begin was called).
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+};
+
 struct tacaw_ctx {
+  Profiler prof;
   int device = 0;
   uint64_t budget = 0;
   std::string err;
@@ -69,6 +83,16 @@ struct Scratch {
   }
 };
 
+
+// Records a CUDA event pair around the launches in its scope when profiling is on.
+struct ProfScope {
+  tacaw_ctx* ctx;
+  cudaStream_t st;
+  ProfRec rec{};
+  bool active = false;
+  ProfScope(tacaw_ctx* c, const char* name, cudaStream_t s, double bytes, double flops);
+  ~ProfScope();
+};
 
 int set_err(tacaw_ctx* c, int code, const char* fmt, ...);
 int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where);

@@ -81,11 +81,11 @@ def test_bin_slices_bit_exact(ctx, T):
 # ------------------------------------------------------------------------------------------
 # a2 projected potential
 # ------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_off"])
+@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_half"])
 def test_potential_parity(ctx, T, case):
     w = {"c1": lambda: workloads.diamond_si(n_frames=2), "rocksalt": small_rocksalt, "rect": rect_diamond,
-         "bl_off": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4)}[case]()
-    kw = {"bandlimit": 0.0} if case == "bl_off" else {}
+         "bl_half": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4)}[case]()
+    kw = {"bandlimit": 0.5} if case == "bl_half" else {}
     ctx.load_form_factors(w.form_Z, w.form_coef)
     p = T.params_of(w, **kw)
     V = ctx.build_potential(p, dev(w.pos[:2]), dev(w.Z)).cpu().numpy()
@@ -116,6 +116,37 @@ def test_unknown_species_is_rejected(ctx, T):
     assert ei.value.code == T.TACAW_EINVAL
     ctx.load_form_factors(w.form_Z, w.form_coef)  # still usable
     ctx.build_potential(T.params_of(w), dev(w.pos), dev(w.Z))
+
+
+@pytest.mark.parametrize("bl", [0.0, 0.8])
+def test_potential_rejects_band_beyond_two_thirds(ctx, T, bl):
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=2)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    with pytest.raises(T.TacawError) as ei:
+        ctx.build_potential(T.params_of(w, bandlimit=bl), dev(w.pos), dev(w.Z))
+    assert ei.value.code == T.TACAW_EINVAL
+
+
+def test_propagate_without_band_limit(ctx, T):
+    # no mask anywhere: the oracle's potential drives both sides, so only a3-a5 are compared
+    w = workloads.diamond_si(n_frames=1, grid=64, n_slices=3)
+    op = oracle.params_of(w, bandlimit=0.0)
+    V = np.stack([oracle.potential_slice(op, w.pos[0], w.Z, s, w.form_Z, w.form_coef) for s in range(3)])
+    V32 = V.astype(np.float32)
+    p = T.params_of(w, bandlimit=0.0)
+    psi = ctx.propagate(p, dev(V32[None]), T.probe_of(w)).cpu().numpy()[0, 0]
+    # oracle multislice from the same float32 V: transmission + slices in FP64
+    t = [oracle.transmission(op, V32[s].astype(np.float64)) for s in range(3)]
+    N = w.nx
+    psi_r = np.full((N, N), 1 / N, complex)
+    k = np.fft.fftfreq(N, d=w.cell[0] / N)
+    k2 = k[:, None] ** 2 + k[None, :] ** 2
+    P = np.exp(-1j * np.pi * oracle.wavelength(100e3) * (w.cell[2] / 3) * k2)
+    for s in range(3):
+        psi_r = oracle.fft2(P * oracle.fft2(t[s] * psi_r, -1) / N ** 2, +1)
+    want = oracle.fft2(psi_r, -1) / N
+    assert rel(psi, want) < TOL_FIELD
+    assert abs(np.sum(np.abs(psi) ** 2) - 1) < 1e-5
 
 
 def test_bad_grid_is_rejected(ctx, T):
