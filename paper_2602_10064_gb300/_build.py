@@ -35,9 +35,14 @@ def _newest_input():
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Build (or reuse) libtacaw.so; returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
+    """Build (or reuse) libtacaw.so; returns its path.  TACAW_NVCC_DEFINES (space-separated
+    -D flags) selects tuning variants of the kernels, e.g. "-DTACAW_FFT_MINB=2"."""
+    defines = os.environ.get("TACAW_NVCC_DEFINES", "").split()
+    stamp = LIB + ".defines"
+    same = os.path.exists(stamp) and open(stamp).read() == " ".join(defines)
+    if not force and same and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
+    extra = list(extra) + defines
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
@@ -60,6 +65,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(" ".join(defines))
     return LIB
 
 

@@ -497,8 +497,29 @@ int64_t chunk_frames(int64_t nf, size_t per_frame, size_t cap) {
 }
 
 // Band-limited transmission of nfs slices from Ap (potential column-pass output) or V.
+// With `compact` (and the transmission band limit on) it stops after the column pass and
+// leaves the compact At [nfs][ny][Wp] in t, for the fused slice row pass; otherwise t is the
+// full [nfs][ny][nx] transmission function.
+bool use_compact_t(const tacaw_params& p, int P) {
+  return P == 1 && p.bandlimit_transmission && p.bandlimit > 0.0;
+}
+
+// Intermediates of the transmission band limit for up to `nfs` slices, allocated once per call.
+struct TransBufs {
+  float2* Bt = nullptr;
+  float2* At = nullptr;
+};
+int trans_bufs(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, int64_t nfs, bool compact, Scratch& sc,
+               TransBufs* tb) {
+  if (!(p.bandlimit_transmission && p.bandlimit > 0.0)) return TACAW_OK;
+  const size_t plane = (size_t)p.ny * g->band.Wp;
+  CK(sc.get(&tb->Bt, (size_t)nfs * plane));
+  if (!compact) CK(sc.get(&tb->At, (size_t)nfs * plane));
+  return TACAW_OK;
+}
+
 int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* Ap, const float* V, int nfs,
-                      float2* t, Scratch& sc) {
+                      float2* t, Scratch& sc, const TransBufs& tb, bool compact = false) {
   const Geo geo{p.nx, p.ny, ctx->tw};
   const float sig = (float)sigma_per_VA(p.voltage_ev);
   const int bl = p.bandlimit_transmission && p.bandlimit > 0.0;
@@ -514,10 +535,8 @@ int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const 
     }
     return TACAW_OK;
   }
-  float2 *Bt, *At;
-  const size_t plane = (size_t)p.ny * g->band.Wp;
-  CK(sc.get(&Bt, (size_t)nfs * plane));
-  CK(sc.get(&At, (size_t)nfs * plane));
+  float2* Bt = tb.Bt;
+  float2* At = compact ? t : tb.At;
   if (Ap) {
     ProfScope ps(ctx, "row_pot_t", sc.st, row * 2 * W8, row * 2 * fx);
     CK(launch_row_pot_out(geo, g->band, Ap, nfs, 1, sig, nullptr, Bt, sc.st));
@@ -529,11 +548,10 @@ int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const 
     ProfScope ps(ctx, "col_t", sc.st, 2.0 * nfs * p.ny * W8, 2.0 * nfs * g->band.W * fy);
     CK(launch_col_t(geo, g->band, Bt, nfs, 1.0f / ((float)p.nx * (float)p.ny), At, sc.st));
   }
-  {
+  if (!compact) {
     ProfScope ps(ctx, "row_tout", sc.st, row * (W8 + 8.0 * p.nx), row * fx);
     CK(launch_row_tout(geo, g->band, At, nfs, t, sc.st));
   }
-  // Bt/At are released with the scratch at the end of the call
   return TACAW_OK;
 }
 
@@ -582,7 +600,7 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
 // Multislice of nfc frames whose transmission functions are t[fl][s][ny][nx]; exit waves go to
 // psi_k[p][f0 + fl] of a [P][F_total][ny][nx] stack (zeroed by the caller).
 int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, int nfc, int P, const float2* psi0,
-           int64_t F_total, int64_t f0, float2* psi_k, Scratch& sc, float2* Apsi, float2* Bpsi) {
+           int64_t F_total, int64_t f0, float2* psi_k, Scratch& sc, float2* Apsi, float2* Bpsi, bool tfused) {
   const Geo geo{p.nx, p.ny, ctx->tw};
   const int S = p.n_slices;
   const float nq = (float)p.nx * (float)p.ny;
@@ -592,10 +610,10 @@ int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, 
     const double W8 = (double)g->band.W * 8.0, rows = (double)P * nfc * p.ny,
                  fx = 5.0 * p.nx * std::log2((double)p.nx), fy = 5.0 * p.ny * std::log2((double)p.ny);
     {
-      const double in = s > 0 ? W8 : (psi0 ? 8.0 * p.nx : 0.0);
-      ProfScope ps(ctx, "slice_row", sc.st, rows * (in + 8.0 * p.nx + W8), rows * (s > 0 ? 2 : 1) * fx);
-      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi,
-                          sc.st));
+      const double in = s > 0 ? W8 : (psi0 ? 8.0 * p.nx : 0.0), tin = tfused ? W8 : 8.0 * p.nx;
+      ProfScope ps(ctx, "slice_row", sc.st, rows * (in + tin + W8), rows * ((s > 0 ? 2 : 1) + (tfused ? 1 : 0)) * fx);
+      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, tfused, Apsi, psi0, t, S, s, P, nfc, plane_amp,
+                          Bpsi, sc.st));
     }
     {
       ProfScope ps(ctx, "slice_col", sc.st, rows * 2 * W8, (double)P * nfc * g->band.W * (last ? 1 : 2) * fy);
@@ -672,11 +690,13 @@ int tacaw_transmission(tacaw_ctx* ctx, const tacaw_params* params, const float* 
   TRY_RC(get_geo(ctx, *params, &g));
   Scratch sc((cudaStream_t)stream);
   const int64_t nfs = nf * params->n_slices;
-  const int64_t step = 4096;
+  const int64_t step = std::min<int64_t>(nfs, 1024);
+  TransBufs tb;
+  TRY_RC(trans_bufs(ctx, *params, g, step, false, sc, &tb));
   for (int64_t i = 0; i < nfs; i += step) {
     const int n = (int)std::min(step, nfs - i);
     const size_t off = (size_t)i * params->ny * params->nx;
-    TRY_RC(transmission_from(ctx, *params, g, nullptr, V + off, n, reinterpret_cast<float2*>(t_out) + off, sc));
+    TRY_RC(transmission_from(ctx, *params, g, nullptr, V + off, n, reinterpret_cast<float2*>(t_out) + off, sc, tb));
   }
   return TACAW_OK;
 }
@@ -708,10 +728,13 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
   CK(sc.get(&t, (size_t)chunk * S * nq));
   CK(sc.get(&Apsi, (size_t)chunk * P * plane));
   CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
+  const bool tf = use_compact_t(p, P);
+  TransBufs tb;
+  TRY_RC(trans_bufs(ctx, p, g, chunk * S, tf, sc, &tb));
   for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
     const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
-    TRY_RC(transmission_from(ctx, p, g, nullptr, V + (size_t)f0 * S * nq, nfc * S, t, sc));
-    TRY_RC(slices(ctx, p, g, t, nfc, P, psi0, nf, f0, psi_k, sc, Apsi, Bpsi));
+    TRY_RC(transmission_from(ctx, p, g, nullptr, V + (size_t)f0 * S * nq, nfc * S, t, sc, tb, tf));
+    TRY_RC(slices(ctx, p, g, t, nfc, P, psi0, nf, f0, psi_k, sc, Apsi, Bpsi, tf));
   }
   return TACAW_OK;
 }
@@ -780,9 +803,12 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   CK(sc.get(&t, (size_t)chunk * S * nq));
   CK(sc.get(&Apsi, (size_t)chunk * P * plane));
   CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
+  const bool tf = use_compact_t(p, P);
+  TransBufs tb;
+  TRY_RC(trans_bufs(ctx, p, g, chunk * S, tf, sc, &tb));
   TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
-    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * S, t, sc));
-    return slices(ctx, p, g, t, nfc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi);
+    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * S, t, sc, tb, tf));
+    return slices(ctx, p, g, t, nfc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
   }));
   TRY_RC(spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc));
   if (!out_dev) {

@@ -6,11 +6,13 @@
 // Stockham autosort FFT whose radix-R butterflies run in registers and whose data exchange
 // between passes goes through shared memory.
 //
-// Thread ownership: a transform of length N is done by T = N / E threads; thread t owns the
-// E elements at positions t + T*e (e = 0..E-1) on entry and on exit, so global loads and
-// stores of a row are coalesced (consecutive t, consecutive addresses).  A pass of radix R
-// (R divides E) runs E/R butterflies per thread; the last pass lands in the owner's own
-// registers, so an N = R1*R2*R3 transform makes two shared-memory exchanges.
+// Thread ownership: a transform of length N is done by a group of T = N / E consecutive
+// threads; thread t owns the E elements at positions t + T*e (e = 0..E-1) on entry and on
+// exit, so global loads and stores of a row are coalesced (consecutive t, consecutive
+// addresses).  A pass of radix R (R divides E) runs E/R butterflies per thread; the last pass
+// lands in the owner's own registers, so an N = R1*R2*R3 transform makes two shared-memory
+// exchanges.  Each group synchronises only itself (__syncwarp, or a named barrier when a
+// transform spans several warps), so the warps of a CTA never wait on one another.
 //
 // Twiddles come from a table tw_N[j] = exp(-2 pi i j / N) built on the host in FP64 and
 // rounded to float; the inverse uses the conjugate.  Transforms are unnormalised.
@@ -138,23 +140,54 @@ __device__ __forceinline__ void dft_r(float2* u) {
   else dft16<SIGN>(u);
 }
 
-// Elements per thread for a transform of length N.
+// Elements per thread for a transform of length N (TACAW_FFT_E8_MIN: smallest N that uses 8
+// elements per thread instead of 16; lengths <= 64 always use 8).
+#ifndef TACAW_FFT_E8_MIN
+#define TACAW_FFT_E8_MIN 4096
+#endif
 template <int N>
 struct FftPlan {
-  static constexpr int E = (N <= 64) ? 8 : 16;
+  static constexpr int E = (N <= 64 || (N >= TACAW_FFT_E8_MIN && N <= 1024)) ? 8 : 16;
   static constexpr int T = N / E;
 };
 
-// Shared-memory index of position x for one row-owned transform: one pad slot per 16 keeps
-// the stride-R writes of the first pass free of bank conflicts.
-struct RowIdx {
-  int base;
-  __device__ __forceinline__ int operator()(int x) const { return base + x + (x >> 4); }
+// Barrier of the whole CTA, for transforms whose threads interleave with other transforms'.
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Barrier of the T threads that share one transform: the warp when T <= 32, else the named
+// barrier `id` (1..15) over T threads (the group's warps are consecutive and aligned).
+template <int T>
+struct GroupSync {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (T <= 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(T) : "memory");
+    }
+  }
+};
+
+// Shared-memory index of position x for one row-owned transform: one pad slot per 16
+// elements (per 8 for N <= 64).  With 64-bit accesses this keeps the own-position reads and
+// the stride-R writes of every pass at (or near) the minimum two wavefronts per warp.
+template <int N>
+struct PadShift {
+  static constexpr int SH = N <= 64 ? 3 : 4;
 };
 template <int N>
-__host__ __device__ constexpr int row_smem_stride() { return N + N / 16; }
+struct RowIdx {
+  static constexpr int SH = PadShift<N>::SH;
+  int base;
+  __device__ __forceinline__ int operator()(int x) const { return base + x + (x >> SH); }
+};
+template <int N>
+__host__ __device__ constexpr int row_smem_stride() { return N + (N >> PadShift<N>::SH); }
 
-// Column-owned transforms: C columns interleaved, column c fastest.
+// Column-owned transforms: C columns interleaved in shared memory, column c fastest (the
+// threads of one transform are spread over warps, so these transforms use BlockSync).
 template <int C>
 struct ColIdx {
   int c;
@@ -162,11 +195,11 @@ struct ColIdx {
 };
 
 // One Stockham pass of radix R; NS = product of earlier radices.
-template <int N, int R, int NS, int SIGN, bool LAST, class Idx>
+template <int N, int R, int NS, int SIGN, bool LAST, class Idx, class Sync>
 __device__ __forceinline__ void fft_pass(float2 (&v)[FftPlan<N>::E], float2* sm, const Idx& idx, int t,
-                                         const float2* __restrict__ tw) {
+                                         const float2* __restrict__ tw, const Sync& sync) {
   constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T, B = E / R;
-  if (!LAST) __syncthreads();  // earlier readers of sm are done
+  if (!LAST) sync();  // earlier readers of the group's scratch are done
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int bi = t + T * b;
@@ -193,42 +226,60 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[FftPlan<N>::E], float2* sm,
     }
   }
   if (!LAST) {
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = sm[idx(t + T * e)];
   }
 }
 
 // Unnormalised length-N transform of the elements owned by this thread (positions t + T e),
-// SIGN = -1 forward, +1 inverse.  All threads of the block must call it together.
-// tw points at the table for length N.
-template <int N, int SIGN, class Idx>
+// SIGN = -1 forward, +1 inverse.  All T threads of the group call it together; sm (through
+// idx) is the group's private scratch; sync is the barrier of the threads sharing it.  tw
+// points at the table for length N.
+template <int N, int SIGN, class Idx, class Sync>
 __device__ __forceinline__ void fft(float2 (&v)[FftPlan<N>::E], float2* sm, const Idx& idx, int t,
-                                    const float2* __restrict__ tw) {
+                                    const float2* __restrict__ tw, const Sync& sync) {
   if constexpr (N == 32) {
-    fft_pass<32, 8, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<32, 4, 8, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<32, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<32, 4, 8, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 64) {
-    fft_pass<64, 8, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<64, 8, 8, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<64, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<64, 8, 8, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (FftPlan<N>::E == 8 && N == 128) {
+    fft_pass<128, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, 4, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, 4, 32, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (FftPlan<N>::E == 8 && N == 256) {
+    fft_pass<256, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, 4, 64, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (FftPlan<N>::E == 8 && N == 512) {
+    fft_pass<512, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, 8, 64, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (FftPlan<N>::E == 8 && N == 1024) {
+    fft_pass<1024, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, 4, 64, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, 4, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 128) {
-    fft_pass<128, 16, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<128, 8, 16, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<128, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, 8, 16, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 256) {
-    fft_pass<256, 16, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<256, 16, 16, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<256, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, 16, 16, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 512) {
-    fft_pass<512, 16, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<512, 16, 16, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<512, 2, 256, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<512, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, 2, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 1024) {
-    fft_pass<1024, 16, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<1024, 16, 16, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<1024, 4, 256, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<1024, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, 4, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 2048) {
-    fft_pass<2048, 16, 1, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<2048, 16, 16, SIGN, false>(v, sm, idx, t, tw);
-    fft_pass<2048, 8, 256, SIGN, true>(v, sm, idx, t, tw);
+    fft_pass<2048, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<2048, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<2048, 8, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else {
     static_assert(N == 32, "unsupported FFT length");
   }

@@ -17,21 +17,31 @@
 
 namespace tacaw {
 
+// Minimum resident CTAs per SM requested from the compiler for the FFT pass kernels.
+#ifndef TACAW_FFT_MINB
+#define TACAW_FFT_MINB 2
+#endif
+
 template <int N>
 struct RowCfg {
   static constexpr int T = FftPlan<N>::T;
-  static constexpr int G = (256 / T) > 32 ? 32 : (256 / T);
-  static constexpr int THREADS = G * T;
+  static constexpr int THREADS = (32 * T) < 256 ? 32 * T : 256;
+  static constexpr int G = THREADS / T;  // rows per CTA, one transform group each
   static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
 };
 
 template <int N>
 struct ColCfg {
   static constexpr int T = FftPlan<N>::T;
-  static constexpr int C = (256 / T) > 32 ? 32 : ((256 / T) < 4 ? 4 : 256 / T);
+  static constexpr int C = (256 / T) > 32 ? 32 : ((256 / T) < 4 ? 4 : 256 / T);  // columns per CTA
   static constexpr int THREADS = C * T;
   static constexpr int SMEM = N * C * (int)sizeof(float2);
 };
+
+template <int T>
+__device__ __forceinline__ GroupSync<T> group_sync(int g) {
+  return GroupSync<T>{1 + g};
+}
 
 // Batch index over (grid.y, grid.z); batches beyond nb return before any barrier.
 __device__ __forceinline__ int batch_index() { return blockIdx.y + gridDim.y * blockIdx.z; }
@@ -173,19 +183,31 @@ __device__ __forceinline__ float es_kernel(float z, float beta) {
 
 constexpr int SPREAD_MAX_W = 16;
 
+// Shared memory of the spreading row pass: per-row accumulators (each element owned by one
+// thread, so the sums are race-free and in candidate order), then the candidate tables.
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+struct SplatSmem {
+  static constexpr int NT = RowCfg<NX>::THREADS, G = RowCfg<NX>::G;
+  static constexpr int ACC = G * NX * 8;
+  static constexpr int TAB = NT * (SPREAD_MAX_W + G) * 4 + NT * 4 * 4;
+  static constexpr int BYTES = (ACC + TAB) > RowCfg<NX>::SMEM ? (ACC + TAB) : RowCfg<NX>::SMEM;
+};
+
+template <int NX>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
                 int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
   constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* sm = reinterpret_cast<float2*>(smraw);
-  // candidate tables alias the FFT scratch (used strictly before the transform)
-  float* phx = reinterpret_cast<float*>(smraw);       // [NT][SPREAD_MAX_W]
-  float* phy = phx + NT * SPREAD_MAX_W;                // [NT][G]
-  int* cx0 = reinterpret_cast<int*>(phy + NT * G);     // [NT] first column of the footprint
-  int* cim = cx0 + NT;                                 // [NT] 1: imaginary part (odd slot)
+  float2* sm = reinterpret_cast<float2*>(smraw);                     // FFT scratch (after spreading)
+  float2* acc = reinterpret_cast<float2*>(smraw);                    // [G][NX]
+  float* phx = reinterpret_cast<float*>(smraw + SplatSmem<NX>::ACC); // [NT][SPREAD_MAX_W]
+  float* phy = phx + NT * SPREAD_MAX_W;                               // [NT][G]
+  float* cfx = phy + NT * G;                                          // [NT] candidate records
+  float* cfy = cfx + NT;
+  int* cx0 = reinterpret_cast<int*>(cfy + NT);                        // first footprint column
+  int* ciy = cx0 + NT;                                                // iy0 | imag << 16
   __shared__ int wtot[NW];
 
   const int bidx = batch_index();
@@ -197,11 +219,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
   const int lo = offs[(size_t)f * (S + 1) + s], hi = offs[(size_t)f * (S + 1) + s + 1];
   const AtomRec* R = recs + (size_t)f * A;
 
-  float2 v[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+  for (int e = 0; e < E; ++e) acc[g * NX + t + T * e] = make_float2(0.f, 0.f);
 
   for (int base = lo; base < hi; base += NT) {
+    // 1. stable compaction of the atoms whose footprint meets rows [y0, y0 + G)
     const int j = base + tid;
     bool cand = false;
     AtomRec r;
@@ -226,41 +248,55 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
     }
     if (cand) {
       const int ci = before + __popc(bal & ((1u << lane) - 1u));
-      const int ix0 = r.ixy & 0xffff, iy0 = r.ixy >> 16;
-      cx0[ci] = (ix0 + 1 - h + geo.nx) & (geo.nx - 1);
-      cim[ci] = (r.jslot >> 24) & 1;
-      for (int d = 0; d < W2; ++d) phx[ci * SPREAD_MAX_W + d] = es_kernel(((float)(d + 1 - h) - r.fx) / (float)h, sk.beta);
-      for (int gg = 0; gg < G; ++gg) {
-        int d = (y0 + gg - iy0 + ny) & (ny - 1);
+      cfx[ci] = r.fx;
+      cfy[ci] = r.fy;
+      cx0[ci] = ((r.ixy & 0xffff) + 1 - h + geo.nx) & (geo.nx - 1);
+      ciy[ci] = (r.ixy >> 16) | (((r.jslot >> 24) & 1) << 16);
+    }
+    __syncthreads();
+    // 2. kernel tables, one entry per thread: phx[c][d] (d < 2h) and phy[c][g]
+    const int per = W2 + G;
+    for (int i = tid; i < total * per; i += NT) {
+      const int c = i / per, k = i - c * per;
+      if (k < W2) {
+        phx[c * SPREAD_MAX_W + k] = es_kernel(((float)(k + 1 - h) - cfx[c]) / (float)h, sk.beta);
+      } else {
+        const int gg = k - W2;
+        int d = (y0 + gg - (ciy[c] & 0xffff) + ny) & (ny - 1);
         if (d > ny / 2) d -= ny;
-        phy[ci * G + gg] = (d >= 1 - h && d <= h) ? es_kernel(((float)d - r.fy) / (float)h, sk.beta) : 0.f;
+        phy[c * G + gg] = (d >= 1 - h && d <= h) ? es_kernel(((float)d - cfy[c]) / (float)h, sk.beta) : 0.f;
       }
     }
     __syncthreads();
+    // 3. taps: thread (g, t) owns columns t + T e; a footprint of 2h columns starting at x0
+    //    meets them at the offsets congruent to t - x0 modulo T
+    float2* arow = acc + g * NX;
     for (int c = 0; c < total; ++c) {
       const float wy = phy[c * G + g];
       if (wy == 0.f) continue;
       const int x0 = cx0[c];
-      const bool im = cim[c] != 0;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int dx = (t + T * e - x0 + geo.nx) & (geo.nx - 1);
-        if (dx < W2) {
-          const float a = wy * phx[c * SPREAD_MAX_W + dx];
-          if (im) v[e].y += a;
-          else v[e].x += a;
-        }
+      const bool im = (ciy[c] >> 16) != 0;
+      const int d = (x0 - t) & (NX - 1);
+      for (int off = (T - d % T) % T; off < W2; off += T) {
+        const int x = (x0 + off) & (NX - 1);
+        const float a = wy * phx[c * SPREAD_MAX_W + off];
+        if (im) arow[x].y += a;
+        else arow[x].x += a;
       }
     }
     __syncthreads();
   }
-  fft<NX, -1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = acc[g * NX + t + T * e];
+  __syncthreads();  // the FFT scratch of one group overlaps the accumulators of the next
+  fft<NX, -1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   store_row_compact<NX>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
 }
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
   constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
@@ -270,6 +306,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
   if (fs >= nbatch) return;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C> idx{c};
+  const BlockSync sync;
   const float2* tw = geo.tw + NY;
   float2 acc[E];
 #pragma unroll
@@ -279,12 +316,12 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
     float2 v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-    fft<NY, -1>(v, sm, idx, t, tw);
+    fft<NY, -1>(v, sm, idx, t, tw, sync);
     const float2* m = mtab + (size_t)pr * NY * b.Wp + cc;
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
   }
-  fft<NY, +1>(acc, sm, idx, t, tw);
+  fft<NY, +1>(acc, sm, idx, t, tw, sync);
   float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = acc[e];
@@ -293,7 +330,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
 // Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
 // t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
   constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
@@ -302,10 +339,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
   const int fs = batch_index();
   if (fs >= nbatch) return;
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
-  const RowIdx idx{g * row_smem_stride<NX>()};
+  const RowIdx<NX> idx{g * row_smem_stride<NX>()};
+  const auto sync = group_sync<T>(g);
   float2 v[E];
   load_row_compact<NX>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1>(v, sm, idx, t, geo.tw + NX);
+  fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
   const size_t row = ((size_t)fs * ny + y) * NX;
   if (mode == 0) {
 #pragma unroll
@@ -323,7 +361,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1>(v, sm, idx, t, geo.tw + NX);
+  fft<NX, -1>(v, sm, idx, t, geo.tw + NX, sync);
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
@@ -331,7 +369,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
 // a3: transmission from a stored V.
 // ============================================================================================
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
              float2* __restrict__ out) {
   constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
@@ -353,13 +391,13 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  fft<NX, -1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
   constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -368,19 +406,20 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
   if (fs >= nbatch) return;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C> idx{c};
+  const BlockSync sync;
   const float2* tw = geo.tw + NY;
   const float2* src = Bt + (size_t)fs * NY * b.Wp + cc;
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-  fft<NY, -1>(v, sm, idx, t, tw);
+  fft<NY, -1>(v, sm, idx, t, tw, sync);
   const int nb = cc < b.W ? b.colnb[cc] : -1;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int n = fftfreq_index(t + T * e, NY);
     v[e] = (abs(n) <= nb) ? scale * v[e] : make_float2(0.f, 0.f);
   }
-  fft<NY, +1>(v, sm, idx, t, tw);
+  fft<NY, +1>(v, sm, idx, t, tw, sync);
   float2* dst = At + (size_t)fs * NY * b.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
@@ -388,7 +427,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
 
 // Row pass out of the band limit: IFFT_x -> t (full row).
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
   constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -398,7 +437,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, At + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  fft<NX, +1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   float2* dst = tout + ((size_t)fs * ny + y) * NX;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[t + T * e] = v[e];
@@ -408,7 +447,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
 // Probe: psi0(k) = A(k) exp(-2 pi i k.r_p) amp, then a unitary inverse transform.
 // ============================================================================================
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey, int P, float amp,
                 float2* __restrict__ Bpr) {
   constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
@@ -425,14 +464,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
     const int row = t + T * e, n = fftfreq_index(row, NY);
     v[e] = (abs(n) <= nb) ? amp * cmul(exv, ey[(size_t)p * NY + row]) : make_float2(0.f, 0.f);
   }
-  fft<NY, +1>(v, sm, ColIdx<C>{c}, t, geo.tw + NY);
+  fft<NY, +1>(v, sm, ColIdx<C>{c}, t, geo.tw + NY, BlockSync{});
   float2* dst = Bpr + (size_t)p * NY * ap.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * ap.Wp] = v[e];
 }
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
   constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -442,7 +481,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, Bpr + ((size_t)p * ny + y) * ap.Wp, ap, t);
-  fft<NX, +1>(v, sm, RowIdx{g * row_smem_stride<NX>()}, t, geo.tw + NX);
+  fft<NX, +1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   float2* dst = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[t + T * e] = scale * v[e];
@@ -450,9 +489,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
 
 // ============================================================================================
 // a4/a5: the slice step.
+// TF: t comes as the compact output of the band-limit column pass (At) and is inverse-
+// transformed here (one wave per frame: no full-size t is written or read).
 // ============================================================================================
-template <int NX, bool FIRST, bool PLANE>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS)
+template <int NX, bool FIRST, bool PLANE, bool TF>
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
                 float2* __restrict__ Bpsi) {
@@ -463,30 +504,39 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS)
   if (w >= nwaves) return;
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   const int p = w / nfc, fl = w - p * nfc;
-  const RowIdx idx{g * row_smem_stride<NX>()};
+  const RowIdx<NX> idx{g * row_smem_stride<NX>()};
+  const auto sync = group_sync<T>(g);
+  float2 tv[E];
+  if (TF) {
+    load_row_compact<NX>(tv, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
+    fft<NX, +1>(tv, sm, idx, t, geo.tw + NX, sync);
+  } else {
+    const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
+#pragma unroll
+    for (int e = 0; e < E; ++e) tv[e] = trow[t + T * e];
+  }
   float2 v[E];
   if (FIRST) {
     if (PLANE) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = make_float2(plane_amp, 0.f);
+      for (int e = 0; e < E; ++e) v[e] = plane_amp * tv[e];
     } else {
       const float2* src = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = src[t + T * e];
+      for (int e = 0; e < E; ++e) v[e] = cmul(src[t + T * e], tv[e]);
     }
   } else {
     load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
-    fft<NX, +1>(v, sm, idx, t, geo.tw + NX);
-  }
-  const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
+    fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = cmul(v[e], trow[t + T * e]);
-  fft<NX, -1>(v, sm, idx, t, geo.tw + NX);
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], tv[e]);
+  }
+  fft<NX, -1>(v, sm, idx, t, geo.tw + NX, sync);
   store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
 }
 
 template <int NY, bool LAST>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
@@ -497,12 +547,13 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
   if (w >= nwaves) return;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C> idx{c};
+  const BlockSync sync;
   const float2* tw = geo.tw + NY;
   const float2* src = Bpsi + (size_t)w * NY * b.Wp + cc;
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-  fft<NY, -1>(v, sm, idx, t, tw);
+  fft<NY, -1>(v, sm, idx, t, tw, sync);
   const int nb = cc < b.W ? b.colnb[cc] : -1;
   const float2 pxc = cc < b.W ? px[cc] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -520,14 +571,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS)
     }
     return;
   }
-  fft<NY, +1>(v, sm, idx, t, tw);
+  fft<NY, +1>(v, sm, idx, t, tw, sync);
   float2* dst = Apsi + (size_t)w * NY * b.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
 }
 
 // ============================================================================================
-// Potential multiplier table (FP64 evaluation, float storage).
+// Potential multiplier table [pair][ny][Wp] (FP64 evaluation, float storage).
 // ============================================================================================
 __device__ double form_factor_f64(const double* c, double q) {
   const double q2 = q * q;
@@ -581,16 +632,10 @@ static cudaError_t prep(K kernel, int smem) {
   }
 
 template <int NX>
-static int splat_smem() {
-  const int tables = RowCfg<NX>::THREADS * (SPREAD_MAX_W + RowCfg<NX>::G + 2) * 4;
-  return tables > RowCfg<NX>::SMEM ? tables : RowCfg<NX>::SMEM;
-}
-
-template <int NX>
 static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A,
                                int S, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
   if (2 * sk.half > SPREAD_MAX_W) return cudaErrorInvalidValue;
-  const int smem = splat_smem<NX>();
+  const int smem = SplatSmem<NX>::BYTES;
   cudaError_t e = prep(k_splat_row<NX>, smem);
   if (e != cudaSuccess) return e;
   const int nb = nfs * npair;
@@ -686,24 +731,30 @@ cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, in
 }
 
 template <int NX>
-static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane, const float2* Apsi,
+static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                                const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
                                float2* Bpsi, cudaStream_t st) {
   const int nw = P * nfc;
   const dim3 grid = batch_grid(g.ny / RowCfg<NX>::G, nw);
   constexpr int TH = RowCfg<NX>::THREADS, SM = RowCfg<NX>::SMEM;
-  if (first && plane)
-    k_slice_row<NX, true, true><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);
-  else if (first)
-    k_slice_row<NX, true, false><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);
-  else
-    k_slice_row<NX, false, false><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);
+#define TACAW_SLICE_ROW(F, PL, TFU) \
+  k_slice_row<NX, F, PL, TFU><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi)
+  if (tfused) {
+    if (first && plane) TACAW_SLICE_ROW(true, true, true);
+    else if (first) TACAW_SLICE_ROW(true, false, true);
+    else TACAW_SLICE_ROW(false, false, true);
+  } else {
+    if (first && plane) TACAW_SLICE_ROW(true, true, false);
+    else if (first) TACAW_SLICE_ROW(true, false, false);
+    else TACAW_SLICE_ROW(false, false, false);
+  }
+#undef TACAW_SLICE_ROW
   return cudaGetLastError();
 }
-cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, const float2* Apsi,
+cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                              const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
                              float2* Bpsi, cudaStream_t st) {
-  TACAW_DISPATCH(g.nx, slice_row_n, g, b, first, plane, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi, st);
+  TACAW_DISPATCH(g.nx, slice_row_n, g, b, first, plane, tfused, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi, st);
 }
 
 template <int NY>

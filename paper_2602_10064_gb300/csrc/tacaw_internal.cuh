@@ -63,8 +63,9 @@ cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, con
                              float2* Bpr, cudaStream_t st);
 cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
                              cudaStream_t st);
-// One slice s for n_waves = P * nfc waves; wave w = p * nfc + fl uses t[(fl * S + s)].
-cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, const float2* Apsi,
+// One slice s for n_waves = P * nfc waves; wave w = p * nfc + fl uses t[(fl * S + s)], full
+// rows, or with tfused the compact band-limit column-pass output, inverse-transformed in place.
+cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                              const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
                              float2* Bpsi, cudaStream_t st);
 // last = 0: Apsi = IFFT_y(P M scale FFT_y(Bpsi)); last = 1: psi_k[p][f0 + fl] = P M scale FFT_y(Bpsi).
