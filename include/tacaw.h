@@ -147,6 +147,11 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
               int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
               void* stream);
 
+/* Wait for all work on the context's device, then report TACAW_ETIMEOUT if any kernel of the
+ * context gave up a bounded wait since the last check (its outputs are then invalid), else
+ * TACAW_OK.  The status is cleared by the check. */
+int tacaw_check(tacaw_ctx* ctx);
+
 /* Diagnostics.  tacaw_profile_begin starts recording a CUDA event pair around every kernel
  * launch of the calls that follow, on the stream each launch uses.  tacaw_profile_end stops,
  * waits for the recorded events and reports per kernel class i < max_n (in first-launch order):

@@ -108,6 +108,7 @@ def lib():
             "tacaw_propagate": (C.c_int, [vp, pp, vp, i64, prp, vp, vp]),
             "tacaw_spectrum": (C.c_int, [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp, vp]),
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
+            "tacaw_check": (C.c_int, [vp]),
             "tacaw_profile_begin": (C.c_int, [vp]),
             "tacaw_profile_end": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)]),
         }
@@ -121,7 +122,7 @@ def lib():
 def exported_symbols():
     return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
-            "tacaw_spectrum", "tacaw_run", "tacaw_profile_begin", "tacaw_profile_end"]
+            "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end"]
 
 
 def _ptr(x):
@@ -209,6 +210,10 @@ def tacaw_run(ctx, params, pos, Z, n_atoms, n_frames, probe: ProbeSpec, precisio
                                        C.byref(probe.c), precision, reduce, _ptr(S_out), _stream(stream)))
 
 
+def tacaw_check(ctx):
+    return _check(ctx, lib().tacaw_check(ctx))
+
+
 def tacaw_profile_begin(ctx):
     return _check(ctx, lib().tacaw_profile_begin(ctx))
 
@@ -255,6 +260,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def check(self):
+        tacaw_check(self.h)
 
     def load_form_factors(self, Z, coef):
         tacaw_load_form_factors(self.h, Z, coef)

@@ -379,7 +379,8 @@ int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
       tw[N + j] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
   if (owned_alloc(ctx, &ctx->tw, tw.size()) != TACAW_OK ||
-      cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      owned_alloc(ctx, &ctx->d_status, 1) != TACAW_OK || cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
     for (void* p : ctx->owned) cudaFree(p);
     delete ctx;
     return TACAW_ECUDA;
@@ -816,6 +817,20 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
     CK(cudaStreamSynchronize(st));
   } else if (!pos_dev && A > 0) {
     CK(cudaStreamSynchronize(st));  // the caller's host positions were read asynchronously
+  }
+  return TACAW_OK;
+}
+
+int tacaw_check(tacaw_ctx* ctx) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaDeviceSynchronize());
+  int st = 0;
+  CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    return set_err(ctx, TACAW_ETIMEOUT, "a kernel's bounded wait ran out (status %d); its results are invalid", st);
   }
   return TACAW_OK;
 }

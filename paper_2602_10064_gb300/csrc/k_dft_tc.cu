@@ -1,11 +1,498 @@
-// Tensor-core (tcgen05) time transform.
+// Tensor-core time transform (Methods, "Workflow Architecture": psi~(k, w) = F_t[psi - <psi>_t],
+// I = |psi~|^2) as a dense real GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// With W = exp(-2 pi i w n / F) = cos - i sin and the residual r_n = psi_n - <psi> (FP64), the
+// complex sum becomes the real product D = A B^T:
+//   rows of D: m = 2w + c (c = 0 real, 1 imaginary part of psi~(w)),
+//   K:         kappa = 2n + c' (c' = 0 real, 1 imaginary part of r_n),
+//   A[2w][2n] = cos, A[2w][2n+1] = sin, A[2w+1][2n] = -sin, A[2w+1][2n+1] = cos,
+//   B[j][2n + c'] = r_c'[n][q_j]   (B is K-major: each q's time series is contiguous).
+// Split precision: A = A_hi + A_lo, B = B_hi + B_lo (BF16 or TF32 parts), and
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 in tensor memory.
+//
+// Kernel: one CTA (4 warps) per 128 x 256 tile of D.  Warp 0 lane 0 streams A and B tiles
+// with TMA (128-byte swizzle) into a 4-stage shared-memory ring; warp 1 lane 0 issues
+// tcgen05.mma (M 128, N 256, K 16 for BF16 / 8 for TF32) into a 256-column FP32 accumulator
+// in TMEM; all four warps then read the accumulator with tcgen05.ld and write
+// S = D[2w]^2 + D[2w+1]^2.  Every wait is bounded (%globaltimer); on expiry the kernel sets
+// the context's status word and leaves without hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "tacaw_api_internal.h"
 
 namespace tacaw {
 
-int spectrum_tc(tacaw_ctx* ctx, const float2*, const double2*, int64_t, int64_t, int64_t, int32_t precision,
-                const int32_t*, int64_t, float*, Scratch&) {
-  return set_err(ctx, TACAW_EINVAL, "precision %d is not available in this build", precision);
+constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4, TC_THREADS = 128;
+constexpr int TC_ROW_BYTES = 128;  // one swizzle span of K per tile row
+constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES, TC_B_BYTES = TC_BN * TC_ROW_BYTES;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+
+// status word codes
+constexpr int TC_ERR_TIMEOUT = 1;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the status word set) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try(bar, parity)) {
+    if (globaltimer() - t0 > TC_TIMEOUT_NS) {
+      atomicExch(status, TC_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // swizzle: 128 B
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 256.
+// a/b format: BF16 = 1 (kind::f16), TF32 = 2 (kind::tf32).
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t ab_format) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(tc_idesc(2)), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(tc_idesc(1)), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One 128 x 256 tile of D per CTA; tiles are numbered with the row block fastest so that the
+// CTAs running together share their B tile through L2.
+// nphase: 1 (hi*hi) or 3 (hi*hi, hi*lo, lo*hi); nkb: K blocks of 128 bytes per phase.
+template <bool TF32>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_dft_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+             const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int mtiles,
+             int nphase, int nkb, int64_t F, int64_t ncols, int64_t nsel, int64_t nq, const int32_t* __restrict__ qsel,
+             float* __restrict__ S, int* __restrict__ status) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), accum = smem_u32(bars + 2 * TC_STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x;
+  const int mt = (int)(tile % mtiles);
+  const int64_t nt = tile / mtiles;
+  const int m0 = mt * TC_BM;
+  const int64_t n0 = nt * TC_BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int total = nphase * nkb;  // K blocks; each holds 4 MMAs of 32 bytes of K
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int issued = 0;
+    for (int kb = 0; kb < total; ++kb) {
+      const int s = kb % TC_STAGES;
+      const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, status)) break;
+      const int phase = kb / nkb, kk = kb % nkb;
+      const CUtensorMap* ma = (phase == 2) ? &mAlo : &mAhi;
+      const CUtensorMap* mb = (phase == 1) ? &mBlo : &mBhi;
+      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
+      const int kx = kk * (TC_ROW_BYTES / (TF32 ? 4 : 2));
+      mbar_expect_tx(full0 + 8 * s, TC_STAGE_BYTES);
+      tma_load_2d(sa, ma, kx, m0, full0 + 8 * s);
+      tma_load_2d(sb, mb, kx, (int)n0, full0 + 8 * s);
+      issued = kb + 1;
+    }
+    // leave no copy in flight: wait for the last stages this thread armed
+    for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % TC_STAGES), (uint32_t)((kb / TC_STAGES) & 1), status);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < total; ++kb) {
+      const int s = kb % TC_STAGES;
+      const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+      if (!mbar_wait(full0 + 8 * s, ph, status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
+#pragma unroll
+      for (int k = 0; k < TC_ROW_BYTES / 32; ++k) {
+        tc_mma<TF32>(tmem, smem_desc_sw128(sa + 32 * k), smem_desc_sw128(sb + 32 * k), (kb | k) != 0);
+      }
+      tc_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+    }
+    tc_commit(accum);  // all MMAs issued by this thread complete -> accumulator ready
+  }
+  __syncwarp();
+
+  // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane of D
+  const bool ready = __all_sync(0xffffffffu, mbar_wait(accum, 0, status));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ready) {
+    const int m = m0 + 32 * warp + lane;  // D row; even lanes hold Re, odd lanes Im
+    const int64_t w = m >> 1;
+    const bool writer = ((lane & 1) == 0) && w < F;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float o = __shfl_xor_sync(0xffffffffu, v[i], 1);
+        v[i] = v[i] * v[i] + o * o;
+      }
+      if (writer) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int64_t J = n0 + c0 + i;
+          if (J < ncols) {
+            const int64_t p = J / nsel, j = J - p * nsel;
+            const int64_t q = qsel ? qsel[j] : j;
+            S[((size_t)p * F + w) * nq + q] = v[i];
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  }
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Residual split: B_hi/B_lo[J][2n + c] for J = p * nsel + j, from r = psi[p][n][q_j] - mean[p][j]
+// (FP64), zero for K pad columns.  32 x 32 (j, n) tile per CTA, transposed through shared memory.
+template <bool TF32>
+__global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict__ psi, const double2* __restrict__ mean,
+                                                        int64_t F, int64_t nq, const int32_t* __restrict__ qsel,
+                                                        int64_t nsel, int64_t P, int kpad2, void* __restrict__ Bhi,
+                                                        void* __restrict__ Blo) {
+  __shared__ float2 hs[32][33], ls[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t J0 = (int64_t)blockIdx.x * 32;
+  const int64_t n0 = (int64_t)blockIdx.y * 32;
+  const int64_t ncols = P * nsel;
+  // phase 1: coalesced along j
+  const int64_t J = J0 + tx;
+  int64_t p = 0, j = 0, q = 0;
+  double2 mu = make_double2(0.0, 0.0);
+  if (J < ncols) {
+    p = J / nsel;
+    j = J - p * nsel;
+    q = qsel ? qsel[j] : j;
+    mu = mean[(size_t)p * nsel + j];
+  }
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t n = n0 + r;
+    float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+    if (J < ncols && n < F) {
+      const float2 v = psi[((size_t)p * F + n) * nq + q];
+      const double re = (double)v.x - mu.x, im = (double)v.y - mu.y;
+      if (TF32) {
+        const float ah = to_tf32((float)re), bh = to_tf32((float)im);
+        h = make_float2(ah, bh);
+        l = make_float2(to_tf32((float)(re - (double)ah)), to_tf32((float)(im - (double)bh)));
+      } else {
+        const __nv_bfloat16 ah = __float2bfloat16_rn((float)re), bh = __float2bfloat16_rn((float)im);
+        h = make_float2(__bfloat162float(ah), __bfloat162float(bh));
+        l = make_float2((float)(re - (double)h.x), (float)(im - (double)h.y));
+      }
+    }
+    hs[r][tx] = h;
+    ls[r][tx] = l;
+  }
+  __syncthreads();
+  // phase 2: each warp writes rows J (contiguous along n)
+  for (int c = ty; c < 32; c += 8) {
+    const int64_t Jw = J0 + c;
+    const int64_t n = n0 + tx;
+    if (Jw >= ncols || 2 * n >= kpad2) continue;
+    const float2 h = hs[tx][c], l = ls[tx][c];
+    if (TF32) {
+      reinterpret_cast<float2*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = h;
+      reinterpret_cast<float2*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = l;
+    } else {
+      __nv_bfloat162 hh, ll;
+      hh.x = __float2bfloat16_rn(h.x);
+      hh.y = __float2bfloat16_rn(h.y);
+      ll.x = __float2bfloat16_rn(l.x);
+      ll.y = __float2bfloat16_rn(l.y);
+      reinterpret_cast<__nv_bfloat162*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = hh;
+      reinterpret_cast<__nv_bfloat162*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = ll;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D row-major [rows][kpad] operand, box = 128 bytes of K by box_rows rows, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, bool tf32, int64_t rows, int64_t kpad, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int esz = tf32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(TC_ROW_BYTES / esz), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+uint16_t bf16_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;
+  return (uint16_t)(u >> 16);
+}
+float bf16_to_f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+// round to TF32 (10 mantissa bits), to nearest, ties away from zero
+float tf32_rna(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+}  // namespace
+
+// DFT operand A (hi, lo) for F frames, from FP64 cos/sin of the exactly reduced angle.
+int get_dft_operands(tacaw_ctx* ctx, int64_t F, bool tf32, int64_t kpad, void** hi, void** lo) {
+  const int64_t key = F * 4 + (tf32 ? 1 : 0);
+  auto it = ctx->dft_ops.find(key);
+  if (it != ctx->dft_ops.end()) {
+    *hi = it->second.first;
+    *lo = it->second.second;
+    return TACAW_OK;
+  }
+  const int64_t M = 2 * F;
+  const size_t esz = tf32 ? 4 : 2, n = (size_t)M * kpad;
+  std::vector<uint8_t> h(n * esz, 0), l(n * esz, 0);
+  for (int64_t w = 0; w < F; ++w)
+    for (int64_t t = 0; t < F; ++t) {
+      const double th = 2.0 * M_PI * (double)((w * t) % F) / (double)F;
+      const double c = std::cos(th), s = std::sin(th);
+      const double vals[4] = {c, s, -s, c};  // [2w][2t], [2w][2t+1], [2w+1][2t], [2w+1][2t+1]
+      const int64_t idx[4] = {(2 * w) * kpad + 2 * t, (2 * w) * kpad + 2 * t + 1, (2 * w + 1) * kpad + 2 * t,
+                              (2 * w + 1) * kpad + 2 * t + 1};
+      for (int e = 0; e < 4; ++e) {
+        if (tf32) {
+          const float hv = tf32_rna((float)vals[e]);
+          const float lv = tf32_rna((float)(vals[e] - (double)hv));
+          std::memcpy(&h[idx[e] * 4], &hv, 4);
+          std::memcpy(&l[idx[e] * 4], &lv, 4);
+        } else {
+          const uint16_t hv = bf16_rn((float)vals[e]);
+          const uint16_t lv = bf16_rn((float)(vals[e] - (double)bf16_to_f(hv)));
+          std::memcpy(&h[idx[e] * 2], &hv, 2);
+          std::memcpy(&l[idx[e] * 2], &lv, 2);
+        }
+      }
+    }
+  void *dh = nullptr, *dl = nullptr;
+  cudaError_t e = cudaMalloc(&dh, h.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dl, l.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dh, h.data(), h.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dl, l.data(), l.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (dh) cudaFree(dh);
+    if (dl) cudaFree(dl);
+    return cuda_err(ctx, e, "DFT operand upload");
+  }
+  ctx->owned.push_back(dh);
+  ctx->owned.push_back(dl);
+  ctx->dft_ops[key] = {dh, dl};
+  *hi = dh;
+  *lo = dl;
+  return TACAW_OK;
+}
+
+int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, int64_t nq,
+                int32_t precision, const int32_t* qsel, int64_t nsel, float* S, Scratch& sc) {
+  const bool tf32 = precision == TACAW_DFT_TF32X3 || precision == TACAW_DFT_TF32;
+  const int nphase = (precision == TACAW_DFT_BF16X3 || precision == TACAW_DFT_TF32X3) ? 3 : 1;
+  const int esz = tf32 ? 4 : 2;
+  const int kblk = TC_ROW_BYTES / esz;                 // K elements per block
+  const int64_t kpad = ((2 * F + kblk - 1) / kblk) * kblk;
+  const int64_t ncols = P * nsel;
+  if (ncols > ((int64_t)1 << 31) - 1 || kpad > (1 << 24)) return set_err(ctx, TACAW_EINVAL, "spectrum too large");
+  if (!encode_fn()) return set_err(ctx, TACAW_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  void *Ahi, *Alo;
+  int rc = get_dft_operands(ctx, F, tf32, kpad, &Ahi, &Alo);
+  if (rc != TACAW_OK) return rc;
+  uint8_t *Bhi, *Blo;
+  cudaError_t e = sc.get(&Bhi, (size_t)ncols * kpad * esz);
+  if (e == cudaSuccess) e = sc.get(&Blo, (size_t)ncols * kpad * esz);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "spectrum operand scratch");
+  {
+    ProfScope ps(ctx, tf32 ? "residual_split_tf32" : "residual_split_bf16", sc.st,
+                 (double)P * F * nsel * 8 + (double)ncols * kpad * esz * 2, (double)P * F * nsel * 4);
+    const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((kpad / 2 + 31) / 32));
+    if (grid.y > 65535) return set_err(ctx, TACAW_EINVAL, "too many frames");
+    if (tf32)
+      k_residual_split<true><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, nq, qsel, nsel, P, (int)kpad, Bhi, Blo);
+    else
+      k_residual_split<false><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, nq, qsel, nsel, P, (int)kpad, Bhi, Blo);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "k_residual_split");
+  }
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if (!make_map(&mAhi, Ahi, tf32, 2 * F, kpad, TC_BM) || !make_map(&mAlo, Alo, tf32, 2 * F, kpad, TC_BM) ||
+      !make_map(&mBhi, Bhi, tf32, ncols, kpad, TC_BN) || !make_map(&mBlo, Blo, tf32, ncols, kpad, TC_BN))
+    return set_err(ctx, TACAW_ECUDA, "tensor map encoding failed");
+  const int mtiles = (int)((2 * F + TC_BM - 1) / TC_BM);
+  const int64_t ntiles = (ncols + TC_BN - 1) / TC_BN;
+  const int64_t tiles = (int64_t)mtiles * ntiles;
+  const int nkb = (int)(kpad / kblk);
+  e = tf32 ? cudaFuncSetAttribute(k_dft_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
+           : cudaFuncSetAttribute(k_dft_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFuncSetAttribute");
+  {
+    const double flops = 8.0 * F * F * (double)ncols * nphase;
+    ProfScope ps(ctx, tf32 ? "dft_tc_tf32" : "dft_tc_bf16", sc.st,
+                 (double)ncols * kpad * esz * (nphase > 1 ? 2 : 1) + (double)ncols * F * 4, flops);
+    if (tf32)
+      k_dft_tc<true><<<(unsigned)tiles, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, nphase, nkb, F,
+                                                                     ncols, nsel, nq, qsel, S, ctx->d_status);
+    else
+      k_dft_tc<false><<<(unsigned)tiles, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, nphase, nkb,
+                                                                      F, ncols, nsel, nq, qsel, S, ctx->d_status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "k_dft_tc");
+  }
+  return TACAW_OK;
 }
 
 }  // namespace tacaw

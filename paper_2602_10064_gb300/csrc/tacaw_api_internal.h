@@ -58,6 +58,8 @@ struct tacaw_ctx {
   uint64_t ff_version = 0;
   std::map<std::vector<double>, std::unique_ptr<GeoCache>> geos;
   std::map<int64_t, float2*> time_tw;
+  std::map<int64_t, std::pair<void*, void*>> dft_ops;  // tensor-core DFT operands (hi, lo) per F and kind
+  int* d_status = nullptr;  // device status word: nonzero after a kernel's bounded wait ran out
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };

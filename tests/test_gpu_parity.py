@@ -329,3 +329,53 @@ def test_config2_sampled_frames(ctx, T):
     refs = oracle.multislice(op, w.pos[frames], w.Z, w.form_Z, w.form_coef)[0]
     for i in range(len(frames)):
         assert rel(psi[i], refs[i]) < TOL_FIELD, rel(psi[i], refs[i])
+
+
+# ------------------------------------------------------------------------------------------
+# a7 on tensor cores: split-precision GEMMs vs the oracle
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("P,F,nq", [(1, 64, 100), (2, 96, 300), (1, 200, 513), (3, 32, 17)])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_spectrum_tensor_core_parity(ctx, T, P, F, nq, prec):
+    psi = workloads.random_exit_waves(P, F, nq, seed=P + F + nq)
+    code = {"bf16x3": T.DFT_BF16X3, "tf32x3": T.DFT_TF32X3}[prec]
+    S = ctx.spectrum(dev(psi), precision=code).cpu().numpy()
+    ctx.check()
+    ref = oracle.spectrum(psi)
+    assert rel(S, ref) < 2e-5, rel(S, ref)
+
+
+def test_spectrum_single_product_is_coarser(ctx, T):
+    # the precision study: one BF16 product loses ~3 digits; the split recovers them
+    psi = workloads.random_exit_waves(1, 128, 256, seed=77)
+    ref = oracle.spectrum(psi)
+    e3 = rel(ctx.spectrum(dev(psi), precision=T.DFT_BF16X3).cpu().numpy(), ref)
+    e1 = rel(ctx.spectrum(dev(psi), precision=T.DFT_BF16).cpu().numpy(), ref)
+    ctx.check()
+    assert e1 > 30 * e3 and e1 < 5e-2
+
+
+def test_run_config1_tensor_core(ctx, T):
+    w = workloads.config1()
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w), precision=T.DFT_BF16X3).cpu().numpy()
+    ctx.check()
+    ref = oracle.tacaw(w)
+    err = rel(S, ref)
+    print(f"config 1, BF16x3 time transform: S rel L2 = {err:.3e}")
+    assert err < TOL_S
+
+
+def test_spectrum_tensor_core_qsel_detector(ctx, T):
+    P, F, nq = 2, 64, 400
+    psi = workloads.random_exit_waves(P, F, nq, seed=15)
+    qs = np.array(sorted(np.random.default_rng(2).choice(nq, 150, replace=False)), np.int32)
+    ref = oracle.spectrum(psi)
+    S = ctx.spectrum(dev(psi), precision=T.DFT_BF16X3, q_sel=dev(qs)).cpu().numpy()
+    SI = ctx.spectrum(dev(psi), precision=T.DFT_BF16X3, reduce=T.REDUCE_DETECTOR, q_sel=dev(qs)).cpu().numpy()
+    ctx.check()
+    mask = np.zeros(nq, bool)
+    mask[qs] = True
+    assert np.abs(S[:, :, ~mask]).max() == 0.0
+    assert rel(S[:, :, mask], ref[:, :, mask]) < 2e-5
+    assert rel(SI, ref[:, :, mask].sum(axis=2)) < 2e-5
