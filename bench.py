@@ -38,16 +38,17 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload(name, seed_offset=0):
+def make_workload(name, seed_offset=0, frames=None):
+    """The named configuration; frames (for small profiling cases) truncates the trajectory."""
     import workloads
     if name == "c1":
-        w = workloads.diamond_si(seed=1 + seed_offset, name="c1-diamond-si-64x128sq")
+        w = workloads.diamond_si(n_frames=frames or 64, seed=1 + seed_offset, name="c1-diamond-si-64x128sq")
     elif name == "c2":
-        w = workloads.config2(seed=2 + seed_offset)
+        w = workloads.config2(n_frames=frames or 1024, seed=2 + seed_offset)
     elif name == "c3":
-        w = workloads.config3(seed=3 + seed_offset)
+        w = workloads.config3(n_frames=frames or 256, seed=3 + seed_offset)
     elif name == "c4":
-        w = workloads.config4(seed=4 + seed_offset)
+        w = workloads.config4(n_frames=frames or 2048, seed=4 + seed_offset)
     else:
         raise SystemExit(f"unknown workload {name}")
     return w
@@ -211,7 +212,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, frames=args.frames)
     import oracle
     oracle.build()
     p = oracle.params_of(w)
@@ -249,11 +250,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
-    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-frames", type=int, default=2)
+    ap.add_argument("--frames", type=int, default=None, help="truncate the trajectory (profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -276,7 +278,7 @@ def main():
         dist.barrier()
     import paper_2602_10064_gb300 as T
 
-    w = make_workload(args.workload, seed_offset=1000 * rank)
+    w = make_workload(args.workload, seed_offset=1000 * rank, frames=args.frames)
     prec = PRECISIONS[args.precision]
     ctx = T.Context(local)
     ctx.load_form_factors(w.form_Z, w.form_coef)
