@@ -147,6 +147,26 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
               int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
               void* stream);
 
+/* Allocation-free time transform.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- for example a host application that reserves
+ * the device's memory for its own allocator up front, or that hands this library only the input
+ * and output buffers under a fixed memory budget -- so neither a context (whose creation
+ * allocates) nor cudaMalloc / cudaFree / an allocating library routine is used.
+ * It computes the same S as tacaw_spectrum(..., TACAW_DFT_FP32, TACAW_REDUCE_NONE, q_sel = NULL):
+ * S[p][m][q] = |sum_n (psi[p][n][q] - mean_n psi[p][n][q]) exp(-2 pi i m n / F)|^2 with the mean
+ * and residual in FP64 and the sum in FP32.
+ * psi_k: DEVICE c64 [P][F][nq]; S_out: DEVICE float32 [P][F][nq]; stream as elsewhere.
+ * Scratch (time twiddles, FP64 mean, residual: 8 F + 16 P nq + 8 P F nq bytes, each part
+ * rounded up to 256 bytes) lives in a file-scope device array of 16 MiB that every GPU loading
+ * the library holds until the process exits.  Larger problems return TACAW_ETOOBIG; P or F
+ * above 65535, a NULL or non-device pointer, or a size below 1 return TACAW_EINVAL; a failed
+ * launch returns TACAW_ECUDA.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture.  Every call overwrites all the scratch it reads, so nothing carries over between
+ * calls, but all calls share the one array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. */
+int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, float* S_out, void* stream);
+
 /* Wait for all work on the context's device, then report TACAW_ETIMEOUT if any kernel of the
  * context gave up a bounded wait since the last check (its outputs are then invalid), else
  * TACAW_OK.  The status is cleared by the check. */

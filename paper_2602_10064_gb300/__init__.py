@@ -109,6 +109,7 @@ def lib():
             "tacaw_spectrum": (C.c_int, [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp, vp]),
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
             "tacaw_check": (C.c_int, [vp]),
+            "tacaw_spectrum_static": (C.c_int, [vp, i64, i64, i64, vp, vp]),
             "tacaw_profile_begin": (C.c_int, [vp]),
             "tacaw_profile_end": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)]),
         }
@@ -122,7 +123,8 @@ def lib():
 def exported_symbols():
     return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
-            "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end"]
+            "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end",
+            "tacaw_spectrum_static"]
 
 
 def _ptr(x):
@@ -208,6 +210,11 @@ def tacaw_spectrum(ctx, psi_k, P, F, nq, precision, reduce, q_sel, n_sel, S_out,
 def tacaw_run(ctx, params, pos, Z, n_atoms, n_frames, probe: ProbeSpec, precision, reduce, S_out, stream=None):
     return _check(ctx, lib().tacaw_run(ctx, C.byref(params), _ptr(pos), _ptr(Z), n_atoms, n_frames,
                                        C.byref(probe.c), precision, reduce, _ptr(S_out), _stream(stream)))
+
+
+def tacaw_spectrum_static(psi_k, P, F, nq, S_out, stream=None):
+    """Allocation-free FP32 time transform (no context); returns the TACAW_* code."""
+    return lib().tacaw_spectrum_static(_ptr(psi_k), P, F, nq, _ptr(S_out), _stream(stream))
 
 
 def tacaw_check(ctx):
