@@ -147,6 +147,56 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
               int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
               void* stream);
 
+/* ---- serving: requests admitted by device-memory footprint, run concurrently ------------ */
+
+/* One TACAW simulation request: the inputs and output of tacaw_run. */
+typedef struct tacaw_request {
+  tacaw_params params;
+  tacaw_probe probe;     /* n_probes = 0 means one plane wave; xy (host) is copied at submission */
+  const float* pos;      /* HOST or DEVICE float32 [F][A][3]: host data is copied at submission,
+                            device data must stay valid until the request has finished */
+  const int32_t* Z;      /* HOST or DEVICE int32 [A], copied at submission */
+  int64_t n_atoms;
+  int64_t n_frames;
+  int32_t precision;     /* TACAW_DFT_* */
+  int32_t reduce;        /* TACAW_REDUCE_* */
+  float* S_out;          /* HOST or DEVICE output laid out as in tacaw_run; written before the
+                            request reports TACAW_OK and must stay valid until then */
+} tacaw_request;
+
+/* State of a request.  Times are seconds on the library's monotonic clock. */
+typedef struct tacaw_result {
+  int32_t status;             /* TACAW_PENDING while queued or running, then TACAW_OK or an error */
+  int32_t pad_;
+  uint64_t footprint_bytes;   /* device memory reserved for the request while it runs */
+  double t_submit, t_admit, t_done;
+} tacaw_result;
+
+/* Queue a request (non-blocking).  The request is checked now (EINVAL as tacaw_run; ETOOBIG if
+ * its footprint exceeds the context's budget).  A worker thread admits queued requests while
+ * their footprints fit the budget and one of the context's serving streams is free, and runs
+ * each on its own stream, so admitted requests overlap on the GPU; later requests are admitted
+ * as memory frees up.  A request that does not fit can be overtaken by smaller ones at most 8
+ * times.  *ticket identifies the request. */
+int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket);
+
+/* TACAW_PENDING while the request is queued or running; otherwise its final status (TACAW_OK,
+ * an error code, or TACAW_ECANCELED), after which the ticket is released.  out (optional)
+ * receives the request's state.  TACAW_ENOTFOUND for unknown or released tickets. */
+int tacaw_poll(tacaw_ctx* ctx, uint64_t ticket, tacaw_result* out);
+
+/* Block until the request finishes or timeout_s passes (< 0: no limit); returns as
+ * tacaw_poll, or TACAW_ETIMEOUT (ticket kept) when the time ran out. */
+int tacaw_wait(tacaw_ctx* ctx, uint64_t ticket, double timeout_s, tacaw_result* out);
+
+/* Cancel a request: a queued one finishes at once with TACAW_ECANCELED; a running one runs to
+ * the end but reports TACAW_ECANCELED (its host output is not written). */
+int tacaw_cancel(tacaw_ctx* ctx, uint64_t ticket);
+
+/* Current serving load: queued and running requests, reserved and budgeted device bytes. */
+int tacaw_serving_stats(tacaw_ctx* ctx, int64_t* queued, int64_t* active, uint64_t* used_bytes,
+                        uint64_t* budget_bytes);
+
 /* Allocation-free time transform.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- for example a host application that reserves
  * the device's memory for its own allocator up front, or that hands this library only the input

@@ -64,6 +64,17 @@ def params_of(w, **kw) -> Params:
     return make_params(**d)
 
 
+class Request(C.Structure):
+    _fields_ = [("params", Params), ("probe", Probe), ("pos", C.c_void_p), ("Z", C.c_void_p),
+                ("n_atoms", C.c_int64), ("n_frames", C.c_int64), ("precision", C.c_int32), ("reduce", C.c_int32),
+                ("S_out", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pad_", C.c_int32), ("footprint_bytes", C.c_uint64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 class ProbeSpec:
     """A tacaw_probe plus the host buffer its xy pointer refers to."""
 
@@ -110,6 +121,12 @@ def lib():
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
             "tacaw_check": (C.c_int, [vp]),
             "tacaw_spectrum_static": (C.c_int, [vp, i64, i64, i64, vp, vp]),
+            "tacaw_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+            "tacaw_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
+            "tacaw_wait": (C.c_int, [vp, C.c_uint64, C.c_double, C.POINTER(Result)]),
+            "tacaw_cancel": (C.c_int, [vp, C.c_uint64]),
+            "tacaw_serving_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_uint64),
+                                              C.POINTER(C.c_uint64)]),
             "tacaw_profile_begin": (C.c_int, [vp]),
             "tacaw_profile_end": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)]),
         }
@@ -124,7 +141,8 @@ def exported_symbols():
     return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
             "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end",
-            "tacaw_spectrum_static"]
+            "tacaw_spectrum_static", "tacaw_submit", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
+            "tacaw_serving_stats"]
 
 
 def _ptr(x):
@@ -215,6 +233,39 @@ def tacaw_run(ctx, params, pos, Z, n_atoms, n_frames, probe: ProbeSpec, precisio
 def tacaw_spectrum_static(psi_k, P, F, nq, S_out, stream=None):
     """Allocation-free FP32 time transform (no context); returns the TACAW_* code."""
     return lib().tacaw_spectrum_static(_ptr(psi_k), P, F, nq, _ptr(S_out), _stream(stream))
+
+
+def make_request(params, pos, Z, n_atoms, n_frames, probe: ProbeSpec, precision, reduce, S_out) -> Request:
+    return Request(params, probe.c, _ptr(pos), _ptr(Z), n_atoms, n_frames, precision, reduce, _ptr(S_out))
+
+
+def tacaw_submit(ctx, req: Request) -> int:
+    t = C.c_uint64()
+    _check(ctx, lib().tacaw_submit(ctx, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def tacaw_poll(ctx, ticket):
+    """(code, Result): code is TACAW_PENDING, TACAW_OK or the request's error."""
+    r = Result()
+    rc = lib().tacaw_poll(ctx, ticket, C.byref(r))
+    return rc, r
+
+
+def tacaw_wait(ctx, ticket, timeout_s=-1.0):
+    r = Result()
+    rc = lib().tacaw_wait(ctx, ticket, float(timeout_s), C.byref(r))
+    return rc, r
+
+
+def tacaw_cancel(ctx, ticket):
+    return lib().tacaw_cancel(ctx, ticket)
+
+
+def tacaw_serving_stats(ctx):
+    q, a, u, b = C.c_int64(), C.c_int64(), C.c_uint64(), C.c_uint64()
+    _check(ctx, lib().tacaw_serving_stats(ctx, C.byref(q), C.byref(a), C.byref(u), C.byref(b)))
+    return q.value, a.value, u.value, b.value
 
 
 def tacaw_check(ctx):

@@ -629,6 +629,87 @@ int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, 
 int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
                   int32_t reduce, const int32_t* qsel, int64_t nsel, float* S_out, Scratch& sc);
 
+// Argument checks shared by tacaw_run and tacaw_submit.
+int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr, const float* pos,
+              const int32_t* Z, int64_t n_atoms, int64_t n_frames, int32_t precision, int32_t reduce,
+              const float* S_out) {
+  TRY_RC(check_params(ctx, params));
+  if (n_atoms < 0 || n_frames < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "bad sizes");
+  if (n_frames > 65535 || pr.n_probes > 65535) return set_err(ctx, TACAW_EINVAL, "frames and probes must be <= 65535");
+  if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  TRY_RC(check_spread_band(ctx, params));
+  if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
+  if (!pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
+  if (!S_out || (!Z && n_atoms > 0)) return set_err(ctx, TACAW_EINVAL, "Z, S_out must not be NULL");
+  if (reduce != TACAW_REDUCE_NONE && reduce != TACAW_REDUCE_DETECTOR) return set_err(ctx, TACAW_EINVAL, "bad reduce");
+  if (precision < TACAW_DFT_FP32 || precision > TACAW_DFT_TF32) return set_err(ctx, TACAW_EINVAL, "bad precision");
+  return TACAW_OK;
+}
+
+// Frames per chunk of a run (bounded scratch; intermediates of a chunk stay near L2).
+int64_t run_chunk(const tacaw_params& p, const GeoCache* g, int P, int64_t F) {
+  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
+  const size_t S = (size_t)p.n_slices;
+  const size_t per_frame = S * nq * 8 + S * plane * 8 * (g->npair + 3) + (size_t)P * plane * 16;
+  return chunk_frames(F, per_frame, (size_t)2 << 30);
+}
+
+// Device bytes a run allocates from the stream-ordered pool (tables cached in the context
+// are not counted), mirroring run_impl; used to admit serving requests.
+uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
+                       int32_t reduce, GeoCache* g) {
+  (void)ctx;
+  const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
+  const int64_t chunk = run_chunk(p, g, P, F);
+  double b = 0;
+  b += (double)F * A * (12 + 16) + (double)F * (S + 1) * 4 + A;     // positions, records, offsets, slots
+  b += chunk * S * plane * 8 * (g->npair + 2);                       // Bp, Ap, Bt
+  b += chunk * S * nq * 8;                                            // t (or At)
+  b += chunk * (double)P * plane * 16;                                // Apsi, Bpsi
+  b += (double)P * nq * 16;                                           // probes
+  b += (double)P * F * nq * 8;                                        // exit waves
+  b += (double)P * g->nsel * 16;                                      // mean
+  const double ncols = (double)P * g->nsel;
+  if (precision == TACAW_DFT_FP32) b += (double)F * ncols * 8;
+  else {
+    const double esz = (precision == TACAW_DFT_TF32X3 || precision == TACAW_DFT_TF32) ? 4 : 2;
+    b += ncols * (2.0 * F + 64) * esz * 2;
+  }
+  b += reduce == TACAW_REDUCE_NONE ? (double)P * F * nq * 4 : (double)P * F * nq * 4 + (double)P * F * 4;
+  return (uint64_t)(b * 1.05) + ((uint64_t)64 << 20);
+}
+
+// The whole path on device buffers, stream-ordered: positions d_pos [F][A][3] (device), Z
+// (host or device), S into d_S (device).  Scratch comes from the stream-ordered pool.
+int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const float* d_pos, const int32_t* Z,
+             bool z_dev, int64_t A, int64_t F, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st) {
+  GeoCache* g;
+  TRY_RC(get_geo(ctx, p, &g));
+  Scratch sc(st);
+  const int P = pr.n_probes, S = p.n_slices;
+  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
+  int8_t* slots;
+  TRY_RC(make_slots(ctx, Z, A, z_dev, sc, &slots));
+  float2* psi0 = nullptr;
+  if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
+  float2* psi_k;
+  CK(sc.get(&psi_k, (size_t)P * F * nq));
+  CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
+  const int64_t chunk = run_chunk(p, g, P, F);
+  float2 *t, *Apsi, *Bpsi;
+  CK(sc.get(&t, (size_t)chunk * S * nq));
+  CK(sc.get(&Apsi, (size_t)chunk * P * plane));
+  CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
+  const bool tf = use_compact_t(p, P);
+  TransBufs tb;
+  TRY_RC(trans_bufs(ctx, p, g, chunk * S, tf, sc, &tb));
+  TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
+    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * S, t, sc, tb, tf));
+    return slices(ctx, p, g, t, nfc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
+  }));
+  return spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc);
+}
+
 }  // namespace tacaw
 
 extern "C" {
@@ -759,25 +840,14 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
               void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  TRY_RC(check_params(ctx, params));
-  const tacaw_params& p = *params;
   tacaw_probe pr = probe ? *probe : tacaw_probe{0.0, 1, 0, nullptr};
-  if (n_atoms < 0 || n_frames < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "bad sizes");
-  if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
-  TRY_RC(check_spread_band(ctx, params));
-  if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
-  if (!pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
-  if (!S_out || (!Z && n_atoms > 0)) return set_err(ctx, TACAW_EINVAL, "Z, S_out must not be NULL");
-  if (reduce != TACAW_REDUCE_NONE && reduce != TACAW_REDUCE_DETECTOR) return set_err(ctx, TACAW_EINVAL, "bad reduce");
+  TRY_RC(check_run(ctx, params, pr, pos, Z, n_atoms, n_frames, precision, reduce, S_out));
+  const tacaw_params& p = *params;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  GeoCache* g;
-  TRY_RC(get_geo(ctx, p, &g));
   Scratch sc(st);
-  const int P = pr.n_probes, S = p.n_slices;
   const int64_t F = n_frames, A = n_atoms;
-  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
-  // inputs
+  const size_t nq = (size_t)p.nx * p.ny;
   const bool pos_dev = A > 0 && is_device_ptr(pos), z_dev = A > 0 && is_device_ptr(Z);
   const float* d_pos = pos;
   if (A > 0 && !pos_dev) {
@@ -786,32 +856,11 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
     CK(cudaMemcpyAsync(tmp, pos, sizeof(float) * F * A * 3, cudaMemcpyHostToDevice, st));
     d_pos = tmp;
   }
-  int8_t* slots;
-  TRY_RC(make_slots(ctx, Z, A, z_dev, sc, &slots));
   const bool out_dev = is_device_ptr(S_out);
-  const size_t out_elems = reduce == TACAW_REDUCE_NONE ? (size_t)P * F * nq : (size_t)P * F;
+  const size_t out_elems = reduce == TACAW_REDUCE_NONE ? (size_t)pr.n_probes * F * nq : (size_t)pr.n_probes * F;
   float* d_S = S_out;
   if (!out_dev) CK(sc.get(&d_S, out_elems));
-  float2* psi0 = nullptr;
-  if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
-  // exit-wave stack
-  float2* psi_k;
-  CK(sc.get(&psi_k, (size_t)P * F * nq));
-  CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
-  const size_t per_frame = (size_t)S * nq * 8 + (size_t)S * plane * 8 * (g->npair + 3) + (size_t)P * plane * 16;
-  const int64_t chunk = chunk_frames(F, per_frame, (size_t)2 << 30);
-  float2 *t, *Apsi, *Bpsi;
-  CK(sc.get(&t, (size_t)chunk * S * nq));
-  CK(sc.get(&Apsi, (size_t)chunk * P * plane));
-  CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
-  const bool tf = use_compact_t(p, P);
-  TransBufs tb;
-  TRY_RC(trans_bufs(ctx, p, g, chunk * S, tf, sc, &tb));
-  TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
-    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * S, t, sc, tb, tf));
-    return slices(ctx, p, g, t, nfc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
-  }));
-  TRY_RC(spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc));
+  TRY_RC(run_impl(ctx, p, pr, d_pos, Z, z_dev, A, F, precision, reduce, d_S, st));
   if (!out_dev) {
     CK(cudaMemcpyAsync(S_out, d_S, sizeof(float) * out_elems, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

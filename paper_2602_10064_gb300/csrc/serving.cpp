@@ -1,8 +1,420 @@
-// Serving loop (tacaw_submit / tacaw_poll).
+// Serving loop: tacaw_submit / tacaw_poll / tacaw_wait / tacaw_cancel.
+//
+// Requests (a trajectory plus geometry, beam and output) are queued on submission; a worker
+// thread admits them while their device-memory footprint fits the context's budget and a
+// stream is free, and runs each admitted request's whole path (tacaw_run's pipeline) on its
+// own stream, so the kernels of concurrently admitted requests overlap on the GPU.  Requests
+// that arrive while others run are admitted as soon as memory and a stream free up
+// (continuous batching).  A request that does not fit may be overtaken by later ones that do,
+// at most kMaxSkips times; after that nothing is admitted ahead of it.  Per-request host
+// timestamps (submission, admission, completion) give latency percentiles.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "tacaw_api_internal.h"
 
 namespace tacaw {
 
-void serving_shutdown(tacaw_ctx*) {}
+namespace {
+constexpr int kStreams = 4;
+constexpr int kMaxSkips = 8;
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+struct Job {
+  uint64_t ticket = 0;
+  tacaw_params params{};
+  tacaw_probe probe{};
+  std::vector<double> probe_xy;
+  int64_t A = 0, F = 0;
+  int32_t precision = 0, reduce = 0;
+  const float* pos_dev = nullptr;  // caller's device positions (kept valid by the caller)
+  float* pos_pinned = nullptr;     // copy of host positions
+  std::vector<int32_t> Z;          // host copy of the species
+  float* S_user = nullptr;
+  bool S_host = false;
+  float* S_pinned = nullptr;
+  size_t out_elems = 0;
+  uint64_t footprint = 0;
+  int skips = 0;
+  // run state
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  float* d_pos_tmp = nullptr;
+  float* d_S_tmp = nullptr;
+  int status = TACAW_PENDING;
+  bool canceled = false;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+struct Serving {
+  tacaw_ctx* ctx = nullptr;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  std::thread worker;
+  bool stop = false;
+  std::deque<std::shared_ptr<Job>> queue;
+  std::vector<std::shared_ptr<Job>> active;
+  std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
+  std::vector<cudaStream_t> free_streams;
+  std::vector<cudaStream_t> all_streams;
+  uint64_t next_ticket = 1, used = 0;
+};
+
+namespace {
+
+void release(Serving& sv, Job& j) {
+  if (j.pos_pinned) cudaFreeHost(j.pos_pinned);
+  if (j.S_pinned) cudaFreeHost(j.S_pinned);
+  j.pos_pinned = j.S_pinned = nullptr;
+  if (j.done) cudaEventDestroy(j.done);
+  j.done = nullptr;
+  if (j.stream) sv.free_streams.push_back(j.stream);
+  j.stream = nullptr;
+}
+
+// Enqueue one admitted request on its stream (no serving lock held).
+int launch(Serving& sv, Job& j) {
+  tacaw_ctx* ctx = sv.ctx;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  const float* d_pos = j.pos_dev;
+  if (j.A > 0 && !d_pos) {
+    e = cudaMallocAsync((void**)&j.d_pos_tmp, sizeof(float) * j.F * j.A * 3, j.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(j.d_pos_tmp, j.pos_pinned, sizeof(float) * j.F * j.A * 3, cudaMemcpyHostToDevice, j.stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "request positions");
+    d_pos = j.d_pos_tmp;
+  }
+  float* d_S = j.S_user;
+  if (j.S_host) {
+    e = cudaMallocAsync((void**)&j.d_S_tmp, sizeof(float) * j.out_elems, j.stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "request output");
+    d_S = j.d_S_tmp;
+  }
+  int rc = run_impl(ctx, j.params, j.probe, d_pos, j.Z.data(), false, j.A, j.F, j.precision, j.reduce, d_S, j.stream);
+  if (rc == TACAW_OK && j.S_host) {
+    e = cudaMemcpyAsync(j.S_pinned, d_S, sizeof(float) * j.out_elems, cudaMemcpyDeviceToHost, j.stream);
+    if (e != cudaSuccess) rc = cuda_err(ctx, e, "request output copy");
+  }
+  if (j.d_pos_tmp) cudaFreeAsync(j.d_pos_tmp, j.stream);
+  if (j.d_S_tmp) cudaFreeAsync(j.d_S_tmp, j.stream);
+  j.d_pos_tmp = j.d_S_tmp = nullptr;
+  if (rc == TACAW_OK) {
+    e = cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(j.done, j.stream);
+    if (e != cudaSuccess) rc = cuda_err(ctx, e, "request completion event");
+  }
+  return rc;
+}
+
+void finish(Serving& sv, Job& j, int status) {
+  if (status == TACAW_OK && j.S_host && !j.canceled) std::memcpy(j.S_user, j.S_pinned, sizeof(float) * j.out_elems);
+  j.status = j.canceled ? TACAW_ECANCELED : status;
+  j.t_done = now_s();
+  sv.used -= j.footprint;
+  release(sv, j);
+}
+
+void worker_loop(Serving* svp) {
+  Serving& sv = *svp;
+  cudaSetDevice(sv.ctx->device);
+  std::unique_lock<std::mutex> lk(sv.mu);
+  while (true) {
+    sv.cv.wait_for(lk, std::chrono::microseconds(200),
+                   [&] { return sv.stop || !sv.queue.empty() || !sv.active.empty(); });
+    // completions
+    for (size_t i = 0; i < sv.active.size();) {
+      Job& j = *sv.active[i];
+      const cudaError_t q = cudaEventQuery(j.done);
+      if (q == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      finish(sv, j, q == cudaSuccess ? TACAW_OK : TACAW_ECUDA);
+      sv.active.erase(sv.active.begin() + i);
+      sv.cv_done.notify_all();
+    }
+    if (sv.stop && sv.active.empty()) break;
+    // admissions: in order; one request that does not fit may be overtaken, at most
+    // kMaxSkips times, after which nothing is admitted ahead of it
+    Job* blocked = nullptr;
+    for (auto it = sv.queue.begin(); !sv.stop && it != sv.queue.end() && !sv.free_streams.empty();) {
+      Job& j = **it;
+      if (sv.used + j.footprint > sv.ctx->budget) {
+        if (blocked || j.skips >= kMaxSkips) break;
+        blocked = &j;
+        ++it;
+        continue;
+      }
+      if (blocked) ++blocked->skips;
+      std::shared_ptr<Job> jp = *it;
+      it = sv.queue.erase(it);
+      j.stream = sv.free_streams.back();
+      sv.free_streams.pop_back();
+      sv.used += j.footprint;
+      j.t_admit = now_s();
+      lk.unlock();
+      const int rc = launch(sv, j);
+      lk.lock();
+      if (rc != TACAW_OK) {
+        finish(sv, j, rc);
+        sv.cv_done.notify_all();
+      } else {
+        sv.active.push_back(jp);
+      }
+      it = sv.queue.begin();
+      blocked = nullptr;
+    }
+  }
+  // drain: requests still queued at shutdown are cancelled
+  for (auto& jp : sv.queue) {
+    jp->canceled = true;
+    jp->status = TACAW_ECANCELED;
+    if (jp->pos_pinned) cudaFreeHost(jp->pos_pinned);
+    if (jp->S_pinned) cudaFreeHost(jp->S_pinned);
+    jp->pos_pinned = jp->S_pinned = nullptr;
+  }
+  sv.queue.clear();
+  sv.cv_done.notify_all();
+}
+
+Serving* serving_of(tacaw_ctx* ctx, int* rc) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (ctx->serving) return ctx->serving;
+  auto* sv = new Serving();
+  sv->ctx = ctx;
+  cudaSetDevice(ctx->device);
+  for (int i = 0; i < kStreams; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      *rc = set_err(ctx, TACAW_ECUDA, "cannot create serving streams");
+      for (cudaStream_t t : sv->all_streams) cudaStreamDestroy(t);
+      delete sv;
+      return nullptr;
+    }
+    sv->all_streams.push_back(s);
+    sv->free_streams.push_back(s);
+  }
+  sv->worker = std::thread(worker_loop, sv);
+  ctx->serving = sv;
+  return sv;
+}
+
+void fill(const Job& j, tacaw_result* out) {
+  if (!out) return;
+  out->status = j.status;
+  out->pad_ = 0;
+  out->footprint_bytes = j.footprint;
+  out->t_submit = j.t_submit;
+  out->t_admit = j.t_admit;
+  out->t_done = j.t_done;
+}
+
+}  // namespace
+
+void serving_shutdown(tacaw_ctx* ctx) {
+  Serving* sv = ctx->serving;
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  for (cudaStream_t s : sv->all_streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  ctx->serving = nullptr;
+  delete sv;
+}
 
 }  // namespace tacaw
+
+using namespace tacaw;
+
+extern "C" {
+
+int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
+  if (!ctx || !req || !ticket) return TACAW_EINVAL;
+  auto j = std::make_shared<Job>();
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    tacaw_probe pr = req->probe;
+    if (pr.n_probes == 0) pr = tacaw_probe{0.0, 1, 0, nullptr};
+    int rc = check_run(ctx, &req->params, pr, req->pos, req->Z, req->n_atoms, req->n_frames, req->precision,
+                       req->reduce, req->S_out);
+    if (rc != TACAW_OK) return rc;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+    j->params = req->params;
+    j->A = req->n_atoms;
+    j->F = req->n_frames;
+    j->precision = req->precision;
+    j->reduce = req->reduce;
+    const size_t nq = (size_t)req->params.nx * req->params.ny;
+    j->out_elems = req->reduce == TACAW_REDUCE_NONE ? (size_t)pr.n_probes * j->F * nq : (size_t)pr.n_probes * j->F;
+    if (pr.xy) j->probe_xy.assign(pr.xy, pr.xy + 2 * (size_t)pr.n_probes);
+    j->probe = pr;
+    j->probe.xy = pr.xy ? j->probe_xy.data() : nullptr;
+    // inputs: host data is copied now; device data must stay valid until the request finishes
+    cudaPointerAttributes a{};
+    const auto on_device = [&](const void* p) {
+      if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    };
+    if (j->A > 0) {
+      if (on_device(req->pos)) {
+        j->pos_dev = req->pos;
+      } else {
+        e = cudaMallocHost((void**)&j->pos_pinned, sizeof(float) * j->F * j->A * 3);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMallocHost");
+        std::memcpy(j->pos_pinned, req->pos, sizeof(float) * j->F * j->A * 3);
+      }
+      j->Z.resize(j->A);
+      if (on_device(req->Z)) e = cudaMemcpy(j->Z.data(), req->Z, sizeof(int32_t) * j->A, cudaMemcpyDeviceToHost);
+      else std::memcpy(j->Z.data(), req->Z, sizeof(int32_t) * j->A);
+      if (e != cudaSuccess) {
+        if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+        return cuda_err(ctx, e, "request species");
+      }
+      for (int64_t i = 0; i < j->A; ++i) {
+        bool known = false;
+        for (int32_t z : ctx->ffZ) known |= (z == j->Z[i]);
+        if (!known) {
+          if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+          return set_err(ctx, TACAW_EINVAL, "atom %lld has Z=%d, not in the form-factor table", (long long)i,
+                         j->Z[i]);
+        }
+      }
+    }
+    j->S_user = req->S_out;
+    j->S_host = !on_device(req->S_out);
+    if (j->S_host) {
+      e = cudaMallocHost((void**)&j->S_pinned, sizeof(float) * j->out_elems);
+      if (e != cudaSuccess) {
+        if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+        return cuda_err(ctx, e, "cudaMallocHost");
+      }
+    }
+    GeoCache* g;
+    rc = get_geo(ctx, j->params, &g);
+    if (rc == TACAW_OK) {
+      j->footprint = run_footprint(ctx, j->params, pr.n_probes, j->F, j->A, j->precision, j->reduce, g);
+      if (j->footprint > ctx->budget)
+        rc = set_err(ctx, TACAW_ETOOBIG, "request needs %llu bytes, the budget is %llu",
+                     (unsigned long long)j->footprint, (unsigned long long)ctx->budget);
+    }
+    if (rc != TACAW_OK) {
+      if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+      if (j->S_pinned) cudaFreeHost(j->S_pinned);
+      return rc;
+    }
+  }
+  int rc = TACAW_OK;
+  Serving* sv = serving_of(ctx, &rc);
+  if (!sv) return rc;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    j->ticket = sv->next_ticket++;
+    j->t_submit = now_s();
+    sv->jobs[j->ticket] = j;
+    sv->queue.push_back(j);
+    *ticket = j->ticket;
+  }
+  sv->cv.notify_all();
+  return TACAW_OK;
+}
+
+int tacaw_poll(tacaw_ctx* ctx, uint64_t ticket, tacaw_result* out) {
+  if (!ctx) return TACAW_EINVAL;
+  Serving* sv = ctx->serving;
+  if (!sv) return TACAW_ENOTFOUND;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return TACAW_ENOTFOUND;
+  fill(*it->second, out);
+  const int st = it->second->status;
+  if (st != TACAW_PENDING) sv->jobs.erase(it);
+  return st;
+}
+
+int tacaw_wait(tacaw_ctx* ctx, uint64_t ticket, double timeout_s, tacaw_result* out) {
+  if (!ctx) return TACAW_EINVAL;
+  Serving* sv = ctx->serving;
+  if (!sv) return TACAW_ENOTFOUND;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return TACAW_ENOTFOUND;
+  std::shared_ptr<Job> j = it->second;
+  const double tmo = (timeout_s < 0 || timeout_s > 1e6) ? 1e6 : timeout_s;
+  const bool ok = sv->cv_done.wait_for(lk, std::chrono::duration<double>(tmo),
+                                       [&] { return j->status != TACAW_PENDING; });
+  fill(*j, out);
+  if (!ok) return TACAW_ETIMEOUT;
+  sv->jobs.erase(ticket);
+  return j->status;
+}
+
+int tacaw_cancel(tacaw_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return TACAW_EINVAL;
+  Serving* sv = ctx->serving;
+  if (!sv) return TACAW_ENOTFOUND;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return TACAW_ENOTFOUND;
+  Job& j = *it->second;
+  if (j.status != TACAW_PENDING) return TACAW_OK;
+  j.canceled = true;
+  for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+    if ((*q)->ticket == ticket) {
+      sv->queue.erase(q);
+      j.status = TACAW_ECANCELED;
+      j.t_done = now_s();
+      if (j.pos_pinned) cudaFreeHost(j.pos_pinned);
+      if (j.S_pinned) cudaFreeHost(j.S_pinned);
+      j.pos_pinned = j.S_pinned = nullptr;
+      sv->cv_done.notify_all();
+      break;
+    }
+  return TACAW_OK;
+}
+
+int tacaw_serving_stats(tacaw_ctx* ctx, int64_t* queued, int64_t* active, uint64_t* used_bytes,
+                        uint64_t* budget_bytes) {
+  if (!ctx) return TACAW_EINVAL;
+  Serving* sv = ctx->serving;
+  if (budget_bytes) *budget_bytes = ctx->budget;
+  if (!sv) {
+    if (queued) *queued = 0;
+    if (active) *active = 0;
+    if (used_bytes) *used_bytes = 0;
+    return TACAW_OK;
+  }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (queued) *queued = (int64_t)sv->queue.size();
+  if (active) *active = (int64_t)sv->active.size();
+  if (used_bytes) *used_bytes = sv->used;
+  return TACAW_OK;
+}
+
+}  // extern "C"

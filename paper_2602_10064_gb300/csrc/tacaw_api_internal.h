@@ -102,6 +102,15 @@ int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out);
 // tensor-core time transform (k_dft_tc.cu)
 int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, int64_t nq,
                 int32_t precision, const int32_t* qsel, int64_t nsel, float* S, Scratch& sc);
+// whole-path pieces (api.cu)
+int get_geo(tacaw_ctx* ctx, const tacaw_params& p, GeoCache** out);
+int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr, const float* pos,
+              const int32_t* Z, int64_t n_atoms, int64_t n_frames, int32_t precision, int32_t reduce,
+              const float* S_out);
+uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
+                       int32_t reduce, GeoCache* g);
+int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const float* d_pos, const int32_t* Z,
+             bool z_dev, int64_t A, int64_t F, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st);
 // serving loop (serving.cpp)
 void serving_shutdown(tacaw_ctx* ctx);
 
