@@ -217,6 +217,11 @@ int tacaw_serving_stats(tacaw_ctx* ctx, int64_t* queued, int64_t* active, uint64
  * other host threads) race and must be serialised by the caller. */
 int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, float* S_out, void* stream);
 
+/* Context option.  "max_chunk_frames": cap on the frames whose waves are propagated together
+ * in one batch of launches (0 = automatic, sized to the L2-resident working set; 1 gives the
+ * plain frame-at-a-time path).  EINVAL for an unknown name or a bad value. */
+int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
+
 /* Wait for all work on the context's device, then report TACAW_ETIMEOUT if any kernel of the
  * context gave up a bounded wait since the last check (its outputs are then invalid), else
  * TACAW_OK.  The status is cleared by the check. */

@@ -120,6 +120,7 @@ def lib():
             "tacaw_spectrum": (C.c_int, [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp, vp]),
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
             "tacaw_check": (C.c_int, [vp]),
+            "tacaw_set_option": (C.c_int, [vp, C.c_char_p, i64]),
             "tacaw_spectrum_static": (C.c_int, [vp, i64, i64, i64, vp, vp]),
             "tacaw_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
             "tacaw_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
@@ -142,7 +143,7 @@ def exported_symbols():
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
             "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end",
             "tacaw_spectrum_static", "tacaw_submit", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
-            "tacaw_serving_stats"]
+            "tacaw_serving_stats", "tacaw_set_option"]
 
 
 def _ptr(x):
@@ -268,6 +269,10 @@ def tacaw_serving_stats(ctx):
     return q.value, a.value, u.value, b.value
 
 
+def tacaw_set_option(ctx, name, value):
+    return _check(ctx, lib().tacaw_set_option(ctx, name.encode(), int(value)))
+
+
 def tacaw_check(ctx):
     return _check(ctx, lib().tacaw_check(ctx))
 
@@ -321,6 +326,9 @@ class Context:
 
     def check(self):
         tacaw_check(self.h)
+
+    def set_option(self, name, value):
+        tacaw_set_option(self.h, name, value)
 
     def load_form_factors(self, Z, coef):
         tacaw_load_form_factors(self.h, Z, coef)

@@ -647,20 +647,20 @@ int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr,
 }
 
 // Frames per chunk of a run (bounded scratch; intermediates of a chunk stay near L2).
-int64_t run_chunk(const tacaw_params& p, const GeoCache* g, int P, int64_t F) {
+int64_t run_chunk(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t F) {
   const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
   const size_t S = (size_t)p.n_slices;
   const size_t per_frame = S * nq * 8 + S * plane * 8 * (g->npair + 3) + (size_t)P * plane * 16;
-  return chunk_frames(F, per_frame, (size_t)2 << 30);
+  const int64_t c = chunk_frames(F, per_frame, (size_t)2 << 30);
+  return ctx->max_chunk_frames > 0 ? std::min<int64_t>(c, ctx->max_chunk_frames) : c;
 }
 
 // Device bytes a run allocates from the stream-ordered pool (tables cached in the context
 // are not counted), mirroring run_impl; used to admit serving requests.
 uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
                        int32_t reduce, GeoCache* g) {
-  (void)ctx;
   const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
-  const int64_t chunk = run_chunk(p, g, P, F);
+  const int64_t chunk = run_chunk(ctx, p, g, P, F);
   double b = 0;
   b += (double)F * A * (12 + 16) + (double)F * (S + 1) * 4 + A;     // positions, records, offsets, slots
   b += chunk * S * plane * 8 * (g->npair + 2);                       // Bp, Ap, Bt
@@ -695,7 +695,7 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
   float2* psi_k;
   CK(sc.get(&psi_k, (size_t)P * F * nq));
   CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
-  const int64_t chunk = run_chunk(p, g, P, F);
+  const int64_t chunk = run_chunk(ctx, p, g, P, F);
   float2 *t, *Apsi, *Bpsi;
   CK(sc.get(&t, (size_t)chunk * S * nq));
   CK(sc.get(&Apsi, (size_t)chunk * P * plane));
@@ -868,6 +868,17 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
     CK(cudaStreamSynchronize(st));  // the caller's host positions were read asynchronously
   }
   return TACAW_OK;
+}
+
+int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
+  if (!ctx || !name) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (std::strcmp(name, "max_chunk_frames") == 0) {
+    if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_chunk_frames must be >= 0");
+    ctx->max_chunk_frames = value;
+    return TACAW_OK;
+  }
+  return set_err(ctx, TACAW_EINVAL, "unknown option '%s'", name);
 }
 
 int tacaw_check(tacaw_ctx* ctx) {
