@@ -379,3 +379,48 @@ def test_spectrum_tensor_core_qsel_detector(ctx, T):
     assert np.abs(S[:, :, ~mask]).max() == 0.0
     assert rel(S[:, :, mask], ref[:, :, mask]) < 2e-5
     assert rel(SI, ref[:, :, mask].sum(axis=2)) < 2e-5
+
+
+# ------------------------------------------------------------------------------------------
+# precision study at the 2048-frame, 2 fs shape: error per energy band
+# ------------------------------------------------------------------------------------------
+def band_errors(S, ref, F, dt_fs):
+    """Relative L2 error of S per band of |E| = h |f| (meV): 0-25, 25-50, 50-100, >100."""
+    f = np.fft.fftfreq(F, d=dt_fs * 1e-3)  # THz
+    E = np.abs(f) * workloads.H_MEV_PS
+    out = {}
+    for lo, hi in ((0, 25), (25, 50), (50, 100), (100, 1e9)):
+        m = (E >= lo) & (E < hi)
+        out[f"{lo}-{hi if hi < 1e9 else 'inf'}"] = rel(S[:, m], ref[:, m])
+    out["all"] = rel(S, ref)
+    return out
+
+
+def test_precision_study_2048_frames(ctx, T):
+    F, nq = 2048, 384
+    psi = workloads.harmonic_exit_waves(1, F, nq)
+    ref = oracle.spectrum(psi)
+    rows = {}
+    for name, code in (("fp32", T.DFT_FP32), ("bf16x3", T.DFT_BF16X3), ("tf32x3", T.DFT_TF32X3),
+                       ("bf16", T.DFT_BF16), ("tf32", T.DFT_TF32)):
+        S = ctx.spectrum(dev(psi), precision=code).cpu().numpy()
+        rows[name] = band_errors(S, ref, F, 2.0)
+    ctx.check()
+    for name, r in rows.items():
+        print(name, " ".join(f"{k}:{v:.2e}" for k, v in r.items()))
+    for name in ("fp32", "bf16x3", "tf32x3"):
+        assert rows[name]["all"] < TOL_S
+    assert rows["bf16"]["all"] > 10 * rows["bf16x3"]["all"]
+
+
+def test_config4_sampled_frames(ctx, T):
+    # the 1024^2, 20-slice geometry at 2 fs: two frames against the oracle
+    w = workloads.config4(n_frames=4)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p = T.params_of(w)
+    frames = [0, 3]
+    V = ctx.build_potential(p, dev(w.pos[frames]), dev(w.Z))
+    psi = ctx.propagate(p, V, T.probe_of(w)).cpu().numpy()[0]
+    refs = oracle.multislice(oracle.params_of(w), w.pos[frames], w.Z, w.form_Z, w.form_coef)[0]
+    for i in range(len(frames)):
+        assert rel(psi[i], refs[i]) < TOL_FIELD, rel(psi[i], refs[i])

@@ -337,3 +337,19 @@ def request_workload(spec: RequestSpec) -> Workload:
         kw = dict(alpha_mrad=30.0, probes=probe_grid(cell[0], cell[1], spec.n_scan))
     return _finish(f"req{spec.rid}", R, Z, cell, modes, spec.n_frames, 5.0, spec.n_slices, spec.grid,
                    0.5, **kw)
+
+
+def harmonic_exit_waves(P, F, nq, bins=(3, 40, 90, 300), amps=(1e-2, 3e-3, 1e-3, 3e-4), elastic=1.0,
+                        noise=1e-5, seed=8):
+    """A seeded exit-wave stack whose time dependence is a few complex exponentials on given
+    DFT bins (one per energy band) over a large static part plus white noise: the shape of
+    a multislice stack with a handful of phonon modes, for per-band precision studies."""
+    rng = np.random.default_rng(seed)
+    n = np.arange(F)
+    base = elastic * (rng.standard_normal((P, 1, nq)) + 1j * rng.standard_normal((P, 1, nq)))
+    psi = np.repeat(base, F, axis=1).astype(np.complex128)
+    for b, a in zip(bins, amps):
+        c = a * (rng.standard_normal((P, 1, nq)) + 1j * rng.standard_normal((P, 1, nq)))
+        psi += c * np.exp(2j * np.pi * b * n / F)[None, :, None]
+    psi += noise * (rng.standard_normal((P, F, nq)) + 1j * rng.standard_normal((P, F, nq)))
+    return psi.astype(np.complex64)
