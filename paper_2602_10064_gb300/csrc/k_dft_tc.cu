@@ -10,12 +10,16 @@
 // Split precision: A = A_hi + A_lo, B = B_hi + B_lo (BF16 or TF32 parts), and
 // D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32 in tensor memory.
 //
-// Kernel: one CTA (4 warps) per 128 x 256 tile of D.  Warp 0 lane 0 streams A and B tiles
+// Kernel: one CTA (10 warps) per 128 x 256 tile of D.  Warp 0 lane 0 streams A and B tiles
 // with TMA (128-byte swizzle) into a 4-stage shared-memory ring; warp 1 lane 0 issues
-// tcgen05.mma (M 128, N 256, K 16 for BF16 / 8 for TF32) into a 256-column FP32 accumulator
-// in TMEM; all four warps then read the accumulator with tcgen05.ld and write
-// S = D[2w]^2 + D[2w+1]^2.  Every wait is bounded (%globaltimer); on expiry the kernel sets
-// the context's status word and leaves without hanging.
+// tcgen05.mma (M 128, N 256, K 16 for BF16 / 8 for TF32) into FP32 accumulators in TMEM.
+// The tensor core rounds the accumulator at every MMA with a bias, so over thousands of
+// K steps (the frames of a long trajectory) the error would grow linearly; instead the MMAs
+// of one chunk of TC_KC K blocks accumulate in TMEM (two 256-column buffers, alternating),
+// and after every chunk warps 2..9 add the chunk's partial sums into FP32 registers on the
+// CUDA cores (round to nearest).  At the end those warps form S = D[2w]^2 + D[2w+1]^2.
+// Every wait is bounded (%globaltimer); on expiry the kernel sets the context's status word
+// and leaves without hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,11 +32,15 @@
 
 namespace tacaw {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4, TC_THREADS = 128;
+constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4;
+constexpr int TC_EPI_WARPS = 8, TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr int TC_KC = 16;            // K blocks (of 4 MMAs) accumulated in TMEM per chunk
+constexpr int TC_EPI_COLS = TC_BN / 2;  // accumulator columns per epilogue thread
 constexpr int TC_ROW_BYTES = 128;  // one swizzle span of K per tile row
 constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES, TC_B_BYTES = TC_BN * TC_ROW_BYTES;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+constexpr int TC_TMEM_COLS = 2 * TC_BN;  // two accumulator buffers
 constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 
 // status word codes
@@ -155,8 +163,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ uint8_t smraw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), accum = smem_u32(bars + 2 * TC_STAGES);
+  // bars: full[S], empty[S], acc_full[2], acc_empty[2], drain; then the TMEM base address
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  const uint32_t drain = smem_u32(bars + 2 * TC_STAGES + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * TC_STAGES), acce0 = smem_u32(bars + 2 * TC_STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tile = blockIdx.x;
   const int mt = (int)(tile % mtiles);
@@ -169,12 +180,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, TC_EPI_WARPS);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_BN)
+                 "r"(TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -183,6 +198,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const int total = nphase * nkb;  // K blocks; each holds 4 MMAs of 32 bytes of K
+  const int nchunk = (total + TC_KC - 1) / TC_KC;
 
   if (warp == 0 && lane == 0) {
     // producer
@@ -205,48 +221,71 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
       mbar_wait(full0 + 8 * (kb % TC_STAGES), (uint32_t)((kb / TC_STAGES) & 1), status);
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    for (int kb = 0; kb < total; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
-      if (!mbar_wait(full0 + 8 * s, ph, status)) break;
+    // MMA issuer: chunk c accumulates into TMEM buffer c & 1
+    bool ok = true;
+    for (int c = 0; c < nchunk && ok; ++c) {
+      const int b = c & 1;
+      if (c >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)(((c >> 1) - 1) & 1), status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
+      const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+      const int kb1 = (c + 1) * TC_KC < total ? (c + 1) * TC_KC : total;
+      for (int kb = c * TC_KC; kb < kb1; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+        if (!mbar_wait(full0 + 8 * s, ph, status)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
 #pragma unroll
-      for (int k = 0; k < TC_ROW_BYTES / 32; ++k) {
-        tc_mma<TF32>(tmem, smem_desc_sw128(sa + 32 * k), smem_desc_sw128(sb + 32 * k), (kb | k) != 0);
+        for (int k = 0; k < TC_ROW_BYTES / 32; ++k)
+          tc_mma<TF32>(d, smem_desc_sw128(sa + 32 * k), smem_desc_sw128(sb + 32 * k), (kb - c * TC_KC) | k);
+        tc_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
       }
-      tc_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+      tc_commit(accf0 + 8 * b);  // this chunk's MMAs complete -> buffer b readable
     }
-    tc_commit(accum);  // all MMAs issued by this thread complete -> accumulator ready
-  }
-  __syncwarp();
-
-  // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane of D
-  const bool ready = __all_sync(0xffffffffu, mbar_wait(accum, 0, status));
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ready) {
-    const int m = m0 + 32 * warp + lane;  // D row; even lanes hold Re, odd lanes Im
-    const int64_t w = m >> 1;
-    const bool writer = ((lane & 1) == 0) && w < F;
-#pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+    // no MMA may be in flight when TMEM is released, also after a timeout
+    tc_commit(drain);
+    mbar_wait(drain, 0, status);
+  } else if (warp >= 2) {
+    // accumulators: warp w owns TMEM lanes 32 (w % 4) .. +31 and columns [128 h, 128 h + 128)
+    const int e = warp - 2, quarter = warp & 3, half = e >> 2;
+    float acc[TC_EPI_COLS];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float o = __shfl_xor_sync(0xffffffffu, v[i], 1);
-        v[i] = v[i] * v[i] + o * o;
+    for (int i = 0; i < TC_EPI_COLS; ++i) acc[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunk; ++c) {
+      const int b = c & 1;
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), status));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * TC_BN + half * TC_EPI_COLS);
+#pragma unroll
+      for (int c0 = 0; c0 < TC_EPI_COLS; c0 += 32) {
+        float v[32];
+        tmem_ld32(base + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[c0 + i] += v[i];
       }
-      if (writer) {
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
+    }
+    if (ok) {
+      // rows m0 + 32 quarter + lane: even lanes hold Re, odd lanes Im of psi~(w)
+      const int m = m0 + 32 * quarter + lane;
+      const int64_t w = m >> 1;
+      const bool writer = ((lane & 1) == 0) && w < F;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int64_t J = n0 + c0 + i;
-          if (J < ncols) {
-            const int64_t p = J / nsel, j = J - p * nsel;
-            const int64_t q = qsel ? qsel[j] : j;
-            S[((size_t)p * F + w) * nq + q] = v[i];
-          }
+      for (int i = 0; i < TC_EPI_COLS; ++i) {
+        const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
+        const float sv = acc[i] * acc[i] + o * o;
+        const int64_t J = n0 + half * TC_EPI_COLS + i;
+        if (writer && J < ncols) {
+          const int64_t p = J / nsel, j = J - p * nsel;
+          const int64_t q = qsel ? qsel[j] : j;
+          S[((size_t)p * F + w) * nq + q] = sv;
         }
       }
     }
@@ -254,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
   }
 }
 
