@@ -140,14 +140,11 @@ __device__ __forceinline__ void dft_r(float2* u) {
   else dft16<SIGN>(u);
 }
 
-// Elements per thread for a transform of length N (TACAW_FFT_E8_MIN: smallest N that uses 8
-// elements per thread instead of 16; lengths <= 64 always use 8).
-#ifndef TACAW_FFT_E8_MIN
-#define TACAW_FFT_E8_MIN 4096
-#endif
-template <int N>
+// Elements per thread (E) for a transform of length N: 8 or 16 (8 for N <= 64).  A kernel
+// picks E per pass direction; T = N / E threads share one transform.
+template <int N, int EPREF>
 struct FftPlan {
-  static constexpr int E = (N <= 64 || (N >= TACAW_FFT_E8_MIN && N <= 1024)) ? 8 : 16;
+  static constexpr int E = (N <= 64) ? 8 : EPREF;
   static constexpr int T = N / E;
 };
 
@@ -195,10 +192,10 @@ struct ColIdx {
 };
 
 // One Stockham pass of radix R; NS = product of earlier radices.
-template <int N, int R, int NS, int SIGN, bool LAST, class Idx, class Sync>
-__device__ __forceinline__ void fft_pass(float2 (&v)[FftPlan<N>::E], float2* sm, const Idx& idx, int t,
+template <int N, int E, int R, int NS, int SIGN, bool LAST, class Idx, class Sync>
+__device__ __forceinline__ void fft_pass(float2 (&v)[E], float2* sm, const Idx& idx, int t,
                                          const float2* __restrict__ tw, const Sync& sync) {
-  constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T, B = E / R;
+  constexpr int T = N / E, B = E / R;
   if (!LAST) sync();  // earlier readers of the group's scratch are done
 #pragma unroll
   for (int b = 0; b < B; ++b) {
@@ -236,50 +233,50 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[FftPlan<N>::E], float2* sm,
 // SIGN = -1 forward, +1 inverse.  All T threads of the group call it together; sm (through
 // idx) is the group's private scratch; sync is the barrier of the threads sharing it.  tw
 // points at the table for length N.
-template <int N, int SIGN, class Idx, class Sync>
-__device__ __forceinline__ void fft(float2 (&v)[FftPlan<N>::E], float2* sm, const Idx& idx, int t,
+template <int N, int SIGN, int E, class Idx, class Sync>
+__device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const Idx& idx, int t,
                                     const float2* __restrict__ tw, const Sync& sync) {
   if constexpr (N == 32) {
-    fft_pass<32, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<32, 4, 8, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<32, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<32, E, 4, 8, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 64) {
-    fft_pass<64, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<64, 8, 8, SIGN, true>(v, sm, idx, t, tw, sync);
-  } else if constexpr (FftPlan<N>::E == 8 && N == 128) {
-    fft_pass<128, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<128, 4, 8, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<128, 4, 32, SIGN, true>(v, sm, idx, t, tw, sync);
-  } else if constexpr (FftPlan<N>::E == 8 && N == 256) {
-    fft_pass<256, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<256, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<256, 4, 64, SIGN, true>(v, sm, idx, t, tw, sync);
-  } else if constexpr (FftPlan<N>::E == 8 && N == 512) {
-    fft_pass<512, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<512, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<512, 8, 64, SIGN, true>(v, sm, idx, t, tw, sync);
-  } else if constexpr (FftPlan<N>::E == 8 && N == 1024) {
-    fft_pass<1024, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1024, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1024, 4, 64, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1024, 4, 256, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<64, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<64, E, 8, 8, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 8 && N == 128) {
+    fft_pass<128, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, E, 4, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, E, 4, 32, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 8 && N == 256) {
+    fft_pass<256, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, E, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, E, 4, 64, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 8 && N == 512) {
+    fft_pass<512, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 8, 64, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 8 && N == 1024) {
+    fft_pass<1024, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 4, 64, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 4, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 128) {
-    fft_pass<128, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<128, 8, 16, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<128, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, E, 8, 16, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 256) {
-    fft_pass<256, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<256, 16, 16, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<256, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, E, 16, 16, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 512) {
-    fft_pass<512, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<512, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<512, 2, 256, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 2, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 1024) {
-    fft_pass<1024, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1024, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1024, 4, 256, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 4, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 2048) {
-    fft_pass<2048, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<2048, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<2048, 8, 256, SIGN, true>(v, sm, idx, t, tw, sync);
+    fft_pass<2048, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<2048, E, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<2048, E, 8, 256, SIGN, true>(v, sm, idx, t, tw, sync);
   } else {
     static_assert(N == 32, "unsupported FFT length");
   }

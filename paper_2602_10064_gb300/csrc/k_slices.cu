@@ -22,9 +22,18 @@ namespace tacaw {
 #define TACAW_FFT_MINB 2
 #endif
 
+// Elements per thread of the row and of the column transforms (8 or 16).
+#ifndef TACAW_ROW_E
+#define TACAW_ROW_E 16
+#endif
+#ifndef TACAW_COL_E
+#define TACAW_COL_E 16
+#endif
+
 template <int N>
 struct RowCfg {
-  static constexpr int T = FftPlan<N>::T;
+  static constexpr int E = FftPlan<N, TACAW_ROW_E>::E;
+  static constexpr int T = N / E;
   static constexpr int THREADS = (32 * T) < 256 ? 32 * T : 256;
   static constexpr int G = THREADS / T;  // rows per CTA, one transform group each
   static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
@@ -32,7 +41,8 @@ struct RowCfg {
 
 template <int N>
 struct ColCfg {
-  static constexpr int T = FftPlan<N>::T;
+  static constexpr int E = FftPlan<N, TACAW_COL_E>::E;
+  static constexpr int T = N / E;
   static constexpr int C = (256 / T) > 32 ? 32 : ((256 / T) < 4 ? 4 : 256 / T);  // columns per CTA
   static constexpr int THREADS = C * T;
   static constexpr int SMEM = N * C * (int)sizeof(float2);
@@ -51,10 +61,10 @@ static dim3 batch_grid(int gx, int64_t nb) {
   return dim3((unsigned)gx, y, z);
 }
 
-template <int N>
-__device__ __forceinline__ void load_row_compact(float2 (&v)[FftPlan<N>::E], const float2* __restrict__ src,
-                                                 const Band& b, int t) {
-  constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T;
+template <int N, int E>
+__device__ __forceinline__ void load_row_compact(float2 (&v)[E], const float2* __restrict__ src, const Band& b,
+                                                 int t) {
+  constexpr int T = N / E;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int c = band_x_col(b, N, t + T * e);
@@ -62,10 +72,10 @@ __device__ __forceinline__ void load_row_compact(float2 (&v)[FftPlan<N>::E], con
   }
 }
 
-template <int N>
-__device__ __forceinline__ void store_row_compact(const float2 (&v)[FftPlan<N>::E], float2* __restrict__ dst,
-                                                  const Band& b, int t) {
-  constexpr int E = FftPlan<N>::E, T = FftPlan<N>::T;
+template <int N, int E>
+__device__ __forceinline__ void store_row_compact(const float2 (&v)[E], float2* __restrict__ dst, const Band& b,
+                                                  int t) {
+  constexpr int T = N / E;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int c = band_x_col(b, N, t + T * e);
@@ -197,7 +207,7 @@ template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
                 int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
-  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
+  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);                     // FFT scratch (after spreading)
@@ -299,7 +309,7 @@ template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
-  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -333,7 +343,7 @@ template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
-  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -372,7 +382,7 @@ template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
              float2* __restrict__ out) {
-  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -399,7 +409,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
-  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -429,7 +439,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
 template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
-  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -450,7 +460,7 @@ template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey, int P, float amp,
                 float2* __restrict__ Bpr) {
-  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int p = batch_index();
@@ -473,7 +483,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
 template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
-  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int p = batch_index();
@@ -492,12 +502,18 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 // TF: t comes as the compact output of the band-limit column pass (At) and is inverse-
 // transformed here (one wave per frame: no full-size t is written or read).
 // ============================================================================================
+// Shared memory of the slice row pass: the FFT scratch, plus (TF) one stashed t row per group.
+template <int NX, bool TF>
+struct SliceRowSmem {
+  static constexpr int BYTES = RowCfg<NX>::SMEM + (TF ? RowCfg<NX>::G * NX * (int)sizeof(float2) : 0);
+};
+
 template <int NX, bool FIRST, bool PLANE, bool TF>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
                 float2* __restrict__ Bpsi) {
-  constexpr int E = FftPlan<NX>::E, T = FftPlan<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int w = batch_index();
@@ -506,30 +522,39 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
   const int p = w / nfc, fl = w - p * nfc;
   const RowIdx<NX> idx{g * row_smem_stride<NX>()};
   const auto sync = group_sync<T>(g);
-  float2 tv[E];
-  if (TF) {
-    load_row_compact<NX>(tv, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
-    fft<NX, +1>(tv, sm, idx, t, geo.tw + NX, sync);
-  } else {
-    const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
-#pragma unroll
-    for (int e = 0; e < E; ++e) tv[e] = trow[t + T * e];
-  }
   float2 v[E];
+  if (FIRST && PLANE && TF) {
+    // constant initial wave: FFT_x(c IFFT_x(At)) = c NX At, no transform needed
+    load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = (plane_amp * (float)NX) * v[e];
+    store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
+    return;
+  }
+  // TF: inverse-transform t first and stash the row (each thread rereads only its own
+  // positions, so no barrier is needed); only one row of the wave is then live in registers
+  float2* tst = reinterpret_cast<float2*>(smraw + RowCfg<NX>::SMEM) + g * NX;
+  if (TF) {
+    load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
+    fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
+#pragma unroll
+    for (int e = 0; e < E; ++e) tst[t + T * e] = v[e];
+  }
+  const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
   if (FIRST) {
     if (PLANE) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = plane_amp * tv[e];
+      for (int e = 0; e < E; ++e) v[e] = plane_amp * (TF ? tst[t + T * e] : trow[t + T * e]);
     } else {
       const float2* src = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = cmul(src[t + T * e], tv[e]);
+      for (int e = 0; e < E; ++e) v[e] = cmul(src[t + T * e], TF ? tst[t + T * e] : trow[t + T * e]);
     }
   } else {
     load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
     fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], tv[e]);
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], TF ? tst[t + T * e] : trow[t + T * e]);
   }
   fft<NX, -1>(v, sm, idx, t, geo.tw + NX, sync);
   store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
@@ -540,7 +565,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
-  constexpr int E = FftPlan<NY>::E, T = FftPlan<NY>::T, C = ColCfg<NY>::C;
+  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int w = batch_index();
@@ -736,9 +761,14 @@ static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane
                                float2* Bpsi, cudaStream_t st) {
   const int nw = P * nfc;
   const dim3 grid = batch_grid(g.ny / RowCfg<NX>::G, nw);
-  constexpr int TH = RowCfg<NX>::THREADS, SM = RowCfg<NX>::SMEM;
-#define TACAW_SLICE_ROW(F, PL, TFU) \
-  k_slice_row<NX, F, PL, TFU><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi)
+  constexpr int TH = RowCfg<NX>::THREADS;
+#define TACAW_SLICE_ROW(F, PL, TFU)                                                                               \
+  do {                                                                                                            \
+    constexpr int SM = SliceRowSmem<NX, TFU>::BYTES;                                                              \
+    cudaError_t e_ = prep(k_slice_row<NX, F, PL, TFU>, SM);                                                       \
+    if (e_ != cudaSuccess) return e_;                                                                             \
+    k_slice_row<NX, F, PL, TFU><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);        \
+  } while (0)
   if (tfused) {
     if (first && plane) TACAW_SLICE_ROW(true, true, true);
     else if (first) TACAW_SLICE_ROW(true, false, true);
