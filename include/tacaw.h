@@ -70,12 +70,22 @@ typedef struct tacaw_params {
   double dt_fs;                   /* frame spacing (fs); sets the frequency axis only */
 } tacaw_params;
 
-/* Illumination. */
+/* Illumination (Discussion, "Beyond Vibrational Spectroscopy": aberration function applied
+ * at probe formation; arbitrary complex wavefronts).  A convergent probe is
+ * psi0(k) = A(k) exp(-i chi(k)) exp(-2 pi i k.r_p) / norm with A = 1 for |k| <= alpha/lambda and
+ * chi(k) = pi lambda k^2 (defocus + astig cos 2(phi_k - astig_angle)) + (pi/2) Cs lambda^3 k^4,
+ * so a positive defocus equals free propagation over that distance. */
 typedef struct tacaw_probe {
-  double alpha_mrad; /* convergence semi-angle; <= 0: plane wave (n_probes must be 1) */
-  int32_t n_probes;  /* P >= 1 */
+  double alpha_mrad;   /* convergence semi-angle; <= 0: plane wave (n_probes must be 1) */
+  int32_t n_probes;    /* P >= 1 */
   int32_t pad_;
-  const double* xy;  /* HOST [P][2] probe positions (A); NULL: one probe at (0, 0) */
+  const double* xy;    /* HOST [P][2] probe positions (A); NULL: all probes at (0, 0) */
+  double defocus;      /* A */
+  double cs_mm;        /* spherical aberration, mm */
+  double astig;        /* two-fold astigmatism, A */
+  double astig_angle;  /* rad */
+  const float* psi0;   /* DEVICE c64 [P][ny][nx]: real-space initial waves to use instead of the
+                          aperture probe (e.g. vortex beams), normalised by the caller; NULL: none */
 } tacaw_probe;
 
 /* Library version string (static storage). */
@@ -146,6 +156,27 @@ int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int
 int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z, int64_t n_atoms,
               int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
               void* stream);
+
+/* ---- TACAW accessors and trajectory averaging ------------------------------------------------ */
+
+/* Spectral diffraction (Methods, "Data Structure Design": I(k, w) at one frequency):
+ * out[p][q] = S[p][m][q] with m = round(f_thz F dt_fs 1e-3) mod F (FFT order), plus S[p][-m][q]
+ * when fold != 0 (energy loss and gain together).  S: DEVICE float32 [P][F][nq]; out: DEVICE
+ * float32 [P][nq].  With the detector-summed SI[P][F] of tacaw_spectrum (nq = 1) this is the
+ * spectrum image at f. */
+int tacaw_spectral_diffraction(tacaw_ctx* ctx, const float* S, int64_t P, int64_t F, int64_t nq, double dt_fs,
+                               double f_thz, int32_t fold, float* out, void* stream);
+
+/* Dispersion along a reciprocal-space path (same section, "dispersion()"): S[p][m] bilinearly
+ * interpolated at the points (kx, ky) (1/A, HOST [npts] each) on the periodic k grid of spacing
+ * (1/Lx, 1/Ly).  S: DEVICE float32 [P][F][ny][nx]; out: DEVICE float32 [P][F][npts]. */
+int tacaw_dispersion(tacaw_ctx* ctx, const float* S, int64_t P, int64_t F, int32_t ny, int32_t nx, double Lx,
+                     double Ly, const double* kx, const double* ky, int32_t npts, float* out, void* stream);
+
+/* Trajectory averaging (Supplement, "Sampling Considerations": average the spectra of
+ * independent trajectories): acc[i] += weight * S[i] in FP64.  S: DEVICE float32 [n];
+ * acc: DEVICE float64 [n]. */
+int tacaw_accumulate(tacaw_ctx* ctx, const float* S, int64_t n, double weight, double* acc, void* stream);
 
 /* ---- serving: requests admitted by device-memory footprint, run concurrently ------------ */
 

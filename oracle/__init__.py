@@ -28,8 +28,10 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so next to the source (gcc, OpenMP, -O2; no -march flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, _SRC, "-lm"],
-                       check=True)
+        # no FP contraction: the FP64 integer decisions (slice index, masks) must round exactly
+        # as written, on every host architecture
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-ffp-contract=off", "-o", tmp,
+                        _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -85,6 +87,14 @@ def lib():
                                                 C.c_int, vp]),
                 "oracle_spectrum": (None, [vp, C.c_int, C.c_int, C.c_long, C.c_int, C.c_int, dp]),
                 "oracle_mean": (None, [vp, C.c_int, C.c_int, C.c_long, vp]),
+                "oracle_freq_bin": (C.c_int, [C.c_double, C.c_int, C.c_double]),
+                "oracle_spectral_diffraction": (None, [dp, C.c_int, C.c_int, C.c_long, C.c_double, C.c_double,
+                                                       C.c_int, dp]),
+                "oracle_dispersion": (None, [dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp,
+                                             dp, C.c_int, dp]),
+                "oracle_probe_aberrated": (None, [pp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                  C.c_double, C.c_double, vp]),
+                "oracle_multislice_frame_init": (C.c_int, [pp, fp, ip, C.c_int, ip, dp, C.c_int, vp, C.c_int, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -247,6 +257,55 @@ def mean(psi):
     m = np.zeros((P, nq), dtype=np.complex128)
     lib().oracle_mean(psi.ctypes.data, P, F, nq, m.ctypes.data)
     return m.reshape((P,) + psi.shape[2:])
+
+
+def freq_bin(f_thz, F, dt_fs):
+    return lib().oracle_freq_bin(float(f_thz), int(F), float(dt_fs))
+
+
+def spectral_diffraction(S, dt_fs, f_thz, fold=False):
+    """map[P][...] = S at the bin of f (plus the bin of -f when fold)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    P, F = S.shape[0], S.shape[1]
+    nq = int(np.prod(S.shape[2:]))
+    out = np.zeros((P, nq))
+    lib().oracle_spectral_diffraction(_p(S, C.c_double), P, F, nq, float(dt_fs), float(f_thz), int(bool(fold)),
+                                      _p(out, C.c_double))
+    return out.reshape((P,) + S.shape[2:])
+
+
+def dispersion(S, cell, kx, ky):
+    """out[P][F][npts]: S[P][F][ny][nx] bilinearly interpolated at the k points (1/A)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    P, F, ny, nx = S.shape
+    kx = np.ascontiguousarray(kx, dtype=np.float64)
+    ky = np.ascontiguousarray(ky, dtype=np.float64)
+    out = np.zeros((P, F, kx.size))
+    lib().oracle_dispersion(_p(S, C.c_double), P, F, ny, nx, float(cell[0]), float(cell[1]), _p(kx, C.c_double),
+                            _p(ky, C.c_double), kx.size, _p(out, C.c_double))
+    return out
+
+
+def probe_aberrated(p: Params, alpha_mrad, xp=0.0, yp=0.0, df=0.0, cs_mm=0.0, a1=0.0, phi_a=0.0):
+    psi = np.zeros((p.ny, p.nx), dtype=np.complex128)
+    lib().oracle_probe_aberrated(C.byref(p), float(alpha_mrad), float(xp), float(yp), float(df), float(cs_mm),
+                                 float(a1), float(phi_a), psi.ctypes.data)
+    return psi
+
+
+def multislice_frame_init(p: Params, pos, Z, form_Z, form_coef, psi0):
+    """psi_k[P][ny][nx] for one frame from real-space initial waves psi0[P][ny][nx]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    tz, tc = _table(form_Z, form_coef)
+    psi0 = _c128(psi0).reshape(-1, p.ny, p.nx)
+    out = np.zeros_like(psi0)
+    rc = lib().oracle_multislice_frame_init(C.byref(p), _p(pos, C.c_float), _p(Z, C.c_int32), pos.shape[0],
+                                            _p(tz, C.c_int32), _p(tc, C.c_double), len(tz), psi0.ctypes.data,
+                                            psi0.shape[0], out.ctypes.data)
+    if rc < 0:
+        raise ValueError("species missing from the form-factor table")
+    return out
 
 
 def tacaw(w, **kw):

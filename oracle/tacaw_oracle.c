@@ -403,3 +403,100 @@ void oracle_mean(const cplx *psi, int P, int F, long nq, cplx *mean) {
             mean[p * nq + q] = m / (double)F;
         }
 }
+
+/* ---- TACAW accessors (Methods, "Data Structure Design": dispersion, spectral diffraction,
+ * spectrum image) and trajectory averaging (Methods, "Molecular Dynamics"; Supplement,
+ * "Sampling Considerations") ---------------------------------------------------------------- */
+
+/* Bin of frequency f (THz) on an F-point axis with spacing dt (fs): round(f F dt), in FFT order. */
+int oracle_freq_bin(double f_thz, int F, double dt_fs) {
+    long m = lround(f_thz * (double)F * dt_fs * 1e-3);
+    m %= F;
+    if (m < 0) m += F;
+    return (int)m;
+}
+
+/* map[p][q] = S[p][m][q] (+ S[p][-m][q] when fold), m the bin of f. */
+void oracle_spectral_diffraction(const double *S, int P, int F, long nq, double dt_fs, double f_thz, int fold,
+                                 double *map) {
+    int m = oracle_freq_bin(f_thz, F, dt_fs), mn = (F - m) % F;
+    for (long p = 0; p < P; p++)
+        for (long q = 0; q < nq; q++) {
+            double v = S[((size_t)p * F + m) * nq + q];
+            if (fold && mn != m) v += S[((size_t)p * F + mn) * nq + q];
+            map[p * nq + q] = v;
+        }
+}
+
+/* S(k, w) along a path: bilinear interpolation of S[p][m][ny][nx] at (kx, ky) (1/A) on the
+ * periodic reciprocal grid (spacing 1/Lx, 1/Ly).  out[p][m][i]. */
+void oracle_dispersion(const double *S, int P, int F, int ny, int nx, double Lx, double Ly, const double *kx,
+                       const double *ky, int npts, double *out) {
+    for (int p = 0; p < P; p++)
+        for (int m = 0; m < F; m++) {
+            const double *plane = S + ((size_t)p * F + m) * (size_t)ny * nx;
+            for (int i = 0; i < npts; i++) {
+                double u = kx[i] * Lx, v = ky[i] * Ly;      /* fractional grid indices */
+                double u0 = floor(u), v0 = floor(v), fu = u - u0, fv = v - v0;
+                long iu = ((long)u0 % nx + nx) % nx, iv = ((long)v0 % ny + ny) % ny;
+                long iu1 = (iu + 1) % nx, iv1 = (iv + 1) % ny;
+                double s00 = plane[iv * nx + iu], s01 = plane[iv * nx + iu1];
+                double s10 = plane[iv1 * nx + iu], s11 = plane[iv1 * nx + iu1];
+                out[((size_t)p * F + m) * npts + i] =
+                    (1 - fv) * ((1 - fu) * s00 + fu * s01) + fv * ((1 - fu) * s10 + fu * s11);
+            }
+        }
+}
+
+/* Convergent probe with aberrations: psi0(k) = A(k) exp(-i chi(k)) exp(-2 pi i k.r_p) / norm,
+ * chi = pi lambda k^2 (df + a1 cos 2(phi - phi_a)) + (pi/2) Cs lambda^3 k^4 (df, a1 in A,
+ * Cs in mm), then a unitary inverse transform.  With chi = 0 this is oracle_probe. */
+void oracle_probe_aberrated(const oracle_params *p, double alpha_mrad, double xp, double yp, double df_A,
+                            double cs_mm, double a1_A, double phi_a, cplx *psi) {
+    const int nx = p->nx, ny = p->ny;
+    const size_t nq = (size_t)nx * ny;
+    const double lam = oracle_wavelength(p->voltage_ev);
+    const double kmax = alpha_mrad * 1e-3 / lam, cs = cs_mm * 1e7;
+    double norm2 = 0.0;
+    for (int iy = 0; iy < ny; iy++)
+        for (int ix = 0; ix < nx; ix++) {
+            double kx = oracle_kfreq(ix, nx, p->Lx), ky = oracle_kfreq(iy, ny, p->Ly);
+            double k2 = kx * kx + ky * ky;
+            int in = k2 <= kmax * kmax;
+            double chi = M_PI * lam * k2 * (df_A + a1_A * cos(2.0 * (atan2(ky, kx) - phi_a))) +
+                         0.5 * M_PI * cs * lam * lam * lam * k2 * k2;
+            psi[(size_t)iy * nx + ix] = in ? cexp(-I * chi) * cexp(-2.0 * M_PI * I * kx * xp) *
+                                                 cexp(-2.0 * M_PI * I * ky * yp)
+                                           : 0.0;
+            norm2 += in;
+        }
+    for (size_t i = 0; i < nq; i++) psi[i] /= sqrt(norm2);
+    oracle_fft2(psi, ny, nx, +1);
+    for (size_t i = 0; i < nq; i++) psi[i] /= sqrt((double)nq);
+}
+
+/* Multislice of one frame from given real-space initial waves psi0[P][ny][nx] (any probe:
+ * aberrated, vortex, ...): psi_k[P][ny][nx] = DFT(psi_exit) / sqrt(Nq).  Returns 0 or -1. */
+int oracle_multislice_frame_init(const oracle_params *p, const float *pos, const int32_t *Z, int n_atoms,
+                                 const int32_t *tabZ, const double *coef, int nZ, const cplx *psi0, int n_probes,
+                                 cplx *psi_k) {
+    const size_t nq = (size_t)p->nx * p->ny;
+    const int S = p->n_slices;
+    double *V = malloc(sizeof(double) * nq);
+    cplx *t = malloc(sizeof(cplx) * nq * (size_t)S);
+    int rc = 0;
+    for (int s = 0; s < S; s++) {
+        if (oracle_potential_slice(p, pos, Z, n_atoms, s, tabZ, coef, nZ, V) < 0) rc = -1;
+        oracle_transmission(p, V, t + nq * (size_t)s);
+    }
+    for (int ip = 0; ip < n_probes; ip++) {
+        cplx *psi = psi_k + nq * (size_t)ip;
+        memcpy(psi, psi0 + nq * (size_t)ip, sizeof(cplx) * nq);
+        for (int s = 0; s < S; s++)
+            slice_step(p, t + nq * (size_t)s, psi, (s < S - 1) || p->final_propagator);
+        oracle_fft2(psi, p->ny, p->nx, -1);
+        for (size_t i = 0; i < nq; i++) psi[i] /= sqrt((double)nq);
+    }
+    free(V); free(t);
+    return rc;
+}

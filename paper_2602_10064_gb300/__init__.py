@@ -44,7 +44,9 @@ class Params(C.Structure):
 
 
 class Probe(C.Structure):
-    _fields_ = [("alpha_mrad", C.c_double), ("n_probes", C.c_int32), ("pad_", C.c_int32), ("xy", C.c_void_p)]
+    _fields_ = [("alpha_mrad", C.c_double), ("n_probes", C.c_int32), ("pad_", C.c_int32), ("xy", C.c_void_p),
+                ("defocus", C.c_double), ("cs_mm", C.c_double), ("astig", C.c_double), ("astig_angle", C.c_double),
+                ("psi0", C.c_void_p)]
 
 
 def make_params(nx, ny, n_slices, cell, voltage_ev=100e3, bandlimit=2.0 / 3.0, bandlimit_transmission=1,
@@ -76,12 +78,18 @@ class Result(C.Structure):
 
 
 class ProbeSpec:
-    """A tacaw_probe plus the host buffer its xy pointer refers to."""
+    """A tacaw_probe plus the buffers its pointers refer to.  psi0: optional device complex64
+    tensor [P][ny][nx] of real-space initial waves used instead of the aperture probe."""
 
-    def __init__(self, alpha_mrad=0.0, xy=None):
+    def __init__(self, alpha_mrad=0.0, xy=None, defocus=0.0, cs_mm=0.0, astig=0.0, astig_angle=0.0, psi0=None):
         self.xy = None if xy is None else np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        self.psi0 = psi0
         n = 1 if self.xy is None else self.xy.shape[0]
-        self.c = Probe(float(alpha_mrad), n, 0, None if self.xy is None else self.xy.ctypes.data)
+        if psi0 is not None:
+            n = psi0.shape[0]
+        self.c = Probe(float(alpha_mrad), n, 0, None if self.xy is None else self.xy.ctypes.data, float(defocus),
+                       float(cs_mm), float(astig), float(astig_angle),
+                       None if psi0 is None else _ptr(psi0))
 
     @property
     def n_probes(self):
@@ -121,6 +129,10 @@ def lib():
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
             "tacaw_check": (C.c_int, [vp]),
             "tacaw_set_option": (C.c_int, [vp, C.c_char_p, i64]),
+            "tacaw_spectral_diffraction": (C.c_int, [vp, vp, i64, i64, i64, C.c_double, C.c_double, i32, vp, vp]),
+            "tacaw_dispersion": (C.c_int, [vp, vp, i64, i64, i32, i32, C.c_double, C.c_double, vp, vp, i32, vp,
+                                           vp]),
+            "tacaw_accumulate": (C.c_int, [vp, vp, i64, C.c_double, vp, vp]),
             "tacaw_spectrum_static": (C.c_int, [vp, i64, i64, i64, vp, vp]),
             "tacaw_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
             "tacaw_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
@@ -143,7 +155,8 @@ def exported_symbols():
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
             "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end",
             "tacaw_spectrum_static", "tacaw_submit", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
-            "tacaw_serving_stats", "tacaw_set_option"]
+            "tacaw_serving_stats", "tacaw_set_option", "tacaw_spectral_diffraction", "tacaw_dispersion",
+            "tacaw_accumulate"]
 
 
 def _ptr(x):
@@ -273,6 +286,22 @@ def tacaw_set_option(ctx, name, value):
     return _check(ctx, lib().tacaw_set_option(ctx, name.encode(), int(value)))
 
 
+def tacaw_spectral_diffraction(ctx, S, P, F, nq, dt_fs, f_thz, fold, out, stream=None):
+    return _check(ctx, lib().tacaw_spectral_diffraction(ctx, _ptr(S), P, F, nq, float(dt_fs), float(f_thz), int(fold),
+                                                        _ptr(out), _stream(stream)))
+
+
+def tacaw_dispersion(ctx, S, P, F, ny, nx, Lx, Ly, kx, ky, out, stream=None):
+    kx = np.ascontiguousarray(kx, dtype=np.float64)
+    ky = np.ascontiguousarray(ky, dtype=np.float64)
+    return _check(ctx, lib().tacaw_dispersion(ctx, _ptr(S), P, F, ny, nx, float(Lx), float(Ly), kx.ctypes.data,
+                                              ky.ctypes.data, kx.size, _ptr(out), _stream(stream)))
+
+
+def tacaw_accumulate(ctx, S, n, weight, acc, stream=None):
+    return _check(ctx, lib().tacaw_accumulate(ctx, _ptr(S), n, float(weight), _ptr(acc), _stream(stream)))
+
+
 def tacaw_check(ctx):
     return _check(ctx, lib().tacaw_check(ctx))
 
@@ -326,6 +355,27 @@ class Context:
 
     def check(self):
         tacaw_check(self.h)
+
+    def spectral_diffraction(self, S, dt_fs, f_thz, fold=False, stream=None):
+        """I(k, w=f) from S[P][F][...] (or the spectrum image from SI[P][F])."""
+        import torch
+        P, F = S.shape[0], S.shape[1]
+        nq = int(math.prod(S.shape[2:])) if S.dim() > 2 else 1
+        out = torch.empty((P,) + tuple(S.shape[2:]), dtype=torch.float32, device=S.device)
+        tacaw_spectral_diffraction(self.h, S, P, F, nq, dt_fs, f_thz, fold, out, stream)
+        return out
+
+    def dispersion(self, S, cell, kx, ky, stream=None):
+        """S[P][F][ny][nx] along the path (kx, ky) (1/A): [P][F][npts]."""
+        import torch
+        P, F, ny, nx = S.shape
+        out = torch.empty((P, F, len(kx)), dtype=torch.float32, device=S.device)
+        tacaw_dispersion(self.h, S, P, F, ny, nx, cell[0], cell[1], kx, ky, out, stream)
+        return out
+
+    def accumulate(self, S, acc, weight=1.0, stream=None):
+        """acc (float64) += weight * S (float32), elementwise on the device."""
+        tacaw_accumulate(self.h, S, S.numel(), weight, acc, stream)
 
     def set_option(self, name, value):
         tacaw_set_option(self.h, name, value)

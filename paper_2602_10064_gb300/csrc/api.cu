@@ -196,6 +196,16 @@ int check_spread_band(tacaw_ctx* ctx, const tacaw_params* p) {
   return TACAW_OK;
 }
 
+tacaw_probe default_probe() {
+  tacaw_probe p{};
+  p.n_probes = 1;
+  return p;
+}
+
+bool has_aberrations(const tacaw_probe& pr) {
+  return pr.defocus != 0.0 || pr.cs_mm != 0.0 || pr.astig != 0.0;
+}
+
 int check_params(tacaw_ctx* ctx, const tacaw_params* p) {
   if (!p) return set_err(ctx, TACAW_EINVAL, "params is NULL");
   if (!pow2_in_range(p->nx) || !pow2_in_range(p->ny))
@@ -580,8 +590,28 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
       ey[(size_t)ip * ny + y] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
   }
+  // aberration phase exp(-i chi(k)) over the aperture columns, FP64 on the host
+  std::vector<float2> chi;
+  if (has_aberrations(pr)) {
+    const double lam = wavelength_A(p.voltage_ev), cs = pr.cs_mm * 1e7;
+    chi.assign((size_t)ny * Wp, make_float2(0.f, 0.f));
+    for (int c = 0; c < W; ++c) {
+      const int x = c <= mb ? c : nx - (W - c);
+      const double kx = kfreq(x, nx, Lx);
+      for (int y = 0; y < ny; ++y) {
+        const double ky = kfreq(y, ny, Ly), k2 = kx * kx + ky * ky;
+        const double ph = M_PI * lam * k2 * (pr.defocus + pr.astig * std::cos(2.0 * (std::atan2(ky, kx) - pr.astig_angle))) +
+                          0.5 * M_PI * cs * lam * lam * lam * k2 * k2;
+        chi[(size_t)y * Wp + c] = make_float2((float)std::cos(ph), (float)-std::sin(ph));
+      }
+    }
+  }
   int* d_nb;
-  float2 *d_ex, *d_ey, *Bpr;
+  float2 *d_ex, *d_ey, *Bpr, *d_chi = nullptr;
+  if (!chi.empty()) {
+    CK(sc.get(&d_chi, chi.size()));
+    CK(cudaMemcpyAsync(d_chi, chi.data(), sizeof(float2) * chi.size(), cudaMemcpyHostToDevice, sc.st));
+  }
   CK(sc.get(&d_nb, Wp));
   CK(sc.get(&d_ex, ex.size()));
   CK(sc.get(&d_ey, ey.size()));
@@ -592,7 +622,7 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
   CK(cudaMemcpyAsync(d_ey, ey.data(), sizeof(float2) * ey.size(), cudaMemcpyHostToDevice, sc.st));
   const Band ap{W, Wp, mb, d_nb};
   const Geo geo{nx, ny, ctx->tw};
-  CK(launch_probe_col(geo, ap, d_ex, d_ey, P, (float)(1.0 / std::sqrt((double)count)), Bpr, sc.st));
+  CK(launch_probe_col(geo, ap, d_ex, d_ey, d_chi, P, (float)(1.0 / std::sqrt((double)count)), Bpr, sc.st));
   CK(launch_probe_row(geo, ap, Bpr, P, (float)(1.0 / std::sqrt((double)nx * ny)), *psi0, sc.st));
   CK(cudaStreamSynchronize(sc.st));  // host tables are local
   return TACAW_OK;
@@ -636,7 +666,9 @@ int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr,
   TRY_RC(check_params(ctx, params));
   if (n_atoms < 0 || n_frames < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "bad sizes");
   if (n_frames > 65535 || pr.n_probes > 65535) return set_err(ctx, TACAW_EINVAL, "frames and probes must be <= 65535");
-  if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  if (pr.alpha_mrad <= 0.0 && !pr.psi0 && pr.n_probes != 1)
+    return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  if (pr.psi0 && !is_device_ptr(pr.psi0)) return set_err(ctx, TACAW_EINVAL, "probe psi0 must be a device pointer");
   TRY_RC(check_spread_band(ctx, params));
   if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
   if (!pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
@@ -691,7 +723,8 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
   int8_t* slots;
   TRY_RC(make_slots(ctx, Z, A, z_dev, sc, &slots));
   float2* psi0 = nullptr;
-  if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
+  if (pr.psi0) psi0 = const_cast<float2*>(reinterpret_cast<const float2*>(pr.psi0));
+  else if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
   float2* psi_k;
   CK(sc.get(&psi_k, (size_t)P * F * nq));
   CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
@@ -789,9 +822,11 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   TRY_RC(check_params(ctx, params));
   const tacaw_params& p = *params;
-  tacaw_probe pr = probe ? *probe : tacaw_probe{0.0, 1, 0, nullptr};
+  tacaw_probe pr = probe ? *probe : default_probe();
   if (nf < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "nf >= 1 and n_probes >= 1 required");
-  if (pr.alpha_mrad <= 0.0 && pr.n_probes != 1) return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  if (pr.alpha_mrad <= 0.0 && !pr.psi0 && pr.n_probes != 1)
+    return set_err(ctx, TACAW_EINVAL, "a plane wave takes exactly one probe");
+  if (pr.psi0 && !is_device_ptr(pr.psi0)) return set_err(ctx, TACAW_EINVAL, "probe psi0 must be a device pointer");
   if (!is_device_ptr(V) || !is_device_ptr(psi_k_out)) return set_err(ctx, TACAW_EINVAL, "V, psi_k_out must be device pointers");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -803,7 +838,8 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
   float2* psi_k = reinterpret_cast<float2*>(psi_k_out);
   CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * nq * P * nf, st));
   float2* psi0 = nullptr;
-  if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
+  if (pr.psi0) psi0 = const_cast<float2*>(reinterpret_cast<const float2*>(pr.psi0));
+  else if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
   const size_t per_frame = (size_t)S * nq * 8 + (size_t)P * plane * 16;
   const int64_t chunk = chunk_frames(nf, per_frame, (size_t)2 << 30);
   float2 *t, *Apsi, *Bpsi;
@@ -840,7 +876,7 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
               void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  tacaw_probe pr = probe ? *probe : tacaw_probe{0.0, 1, 0, nullptr};
+  tacaw_probe pr = probe ? *probe : default_probe();
   TRY_RC(check_run(ctx, params, pr, pos, Z, n_atoms, n_frames, precision, reduce, S_out));
   const tacaw_params& p = *params;
   CK(cudaSetDevice(ctx->device));

@@ -458,8 +458,8 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 // ============================================================================================
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
-    k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey, int P, float amp,
-                float2* __restrict__ Bpr) {
+    k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey,
+                const float2* __restrict__ chi, int P, float amp, float2* __restrict__ Bpr) {
   constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
   for (int e = 0; e < E; ++e) {
     const int row = t + T * e, n = fftfreq_index(row, NY);
     v[e] = (abs(n) <= nb) ? amp * cmul(exv, ey[(size_t)p * NY + row]) : make_float2(0.f, 0.f);
+    if (chi && abs(n) <= nb) v[e] = cmul(v[e], chi[(size_t)row * ap.Wp + cc]);
   }
   fft<NY, +1>(v, sm, ColIdx<C>{c}, t, geo.tw + NY, BlockSync{});
   float2* dst = Bpr + (size_t)p * NY * ap.Wp + cc;
@@ -732,15 +733,15 @@ cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int n
 }
 
 template <int NY>
-static cudaError_t probe_col_n(const Geo& g, const Band& ap, const float2* ex, const float2* ey, int P, float amp,
-                               float2* Bpr, cudaStream_t st) {
+static cudaError_t probe_col_n(const Geo& g, const Band& ap, const float2* ex, const float2* ey, const float2* chi,
+                               int P, float amp, float2* Bpr, cudaStream_t st) {
   k_probe_col<NY><<<batch_grid(ap.Wp / ColCfg<NY>::C, P), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(
-      g, ap, ex, ey, P, amp, Bpr);
+      g, ap, ex, ey, chi, P, amp, Bpr);
   return cudaGetLastError();
 }
-cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, int P, float amp,
-                             float2* Bpr, cudaStream_t st) {
-  TACAW_DISPATCH(g.ny, probe_col_n, g, ap, ex, ey, P, amp, Bpr, st);
+cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, const float2* chi,
+                             int P, float amp, float2* Bpr, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, probe_col_n, g, ap, ex, ey, chi, P, amp, Bpr, st);
 }
 
 template <int NX>

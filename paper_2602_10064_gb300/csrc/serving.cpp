@@ -257,7 +257,10 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
   {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     tacaw_probe pr = req->probe;
-    if (pr.n_probes == 0) pr = tacaw_probe{0.0, 1, 0, nullptr};
+    if (pr.n_probes == 0) {
+      pr = tacaw_probe{};
+      pr.n_probes = 1;
+    }
     int rc = check_run(ctx, &req->params, pr, req->pos, req->Z, req->n_atoms, req->n_frames, req->precision,
                        req->reduce, req->S_out);
     if (rc != TACAW_OK) return rc;

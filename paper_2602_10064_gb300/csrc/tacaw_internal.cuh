@@ -59,8 +59,9 @@ cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, 
 cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
                          cudaStream_t st);
 cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st);
-cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, int P, float amp,
-                             float2* Bpr, cudaStream_t st);
+// chi (nullable): exp(-i chi(k)) over [ny][ap.Wp]
+cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, const float2* chi,
+                             int P, float amp, float2* Bpr, cudaStream_t st);
 cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
                              cudaStream_t st);
 // One slice s for n_waves = P * nfc waves; wave w = p * nfc + fl uses t[(fl * S + s)], full
@@ -89,5 +90,12 @@ cudaError_t launch_dft_fp32(const float2* r, const float2* twF, int64_t P, int64
 // SI[p][m] = sum_j S[p][m][qsel[j]] (FP64 accumulation, deterministic)
 cudaError_t launch_detector_reduce(const float* S, int64_t P, int64_t F, int64_t nq, const int32_t* qsel,
                                    int64_t nsel, float* SI, cudaStream_t st);
+
+// ---- accessors (k_accessors.cu) ------------------------------------------------------------
+cudaError_t launch_spectral_diffraction(const float* S, int64_t P, int64_t F, int64_t nq, int m, int fold,
+                                        float* out, cudaStream_t st);
+cudaError_t launch_dispersion(const float* S, int64_t P, int64_t F, int ny, int nx, const double* u,
+                              const double* v, int npts, float* out, cudaStream_t st);
+cudaError_t launch_accumulate(const float* S, int64_t n, double weight, double* acc, cudaStream_t st);
 
 }  // namespace tacaw

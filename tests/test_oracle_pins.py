@@ -409,3 +409,56 @@ def test_final_propagator_does_not_change_spectrum():
     S1 = oracle.tacaw(w)
     S0 = oracle.tacaw(w, final_propagator=0)
     assert rel(S0, S1) < 1e-10
+
+
+# ---------------------------------------------------------------------------------------
+# accessors, averaging, aberrated probe
+# ---------------------------------------------------------------------------------------
+def test_freq_bin_and_spectral_diffraction():
+    # 200 frames at 10 fs: bins of 0.5 THz (Supplement, "Minimal Working Example")
+    assert oracle.freq_bin(15.0, 200, 10.0) == 30
+    assert oracle.freq_bin(-15.0, 200, 10.0) == 170
+    S = np.random.default_rng(3).random((2, 8, 4, 5))
+    m = oracle.spectral_diffraction(S, 10.0, 2 * 12.5, fold=False)  # F = 8, dt 10 fs: 12.5 THz bins
+    assert np.array_equal(m, S[:, 2])
+    mf = oracle.spectral_diffraction(S, 10.0, 2 * 12.5, fold=True)
+    assert np.allclose(mf, S[:, 2] + S[:, 6])
+
+
+def test_dispersion_interpolation():
+    rng = np.random.default_rng(4)
+    S = rng.random((1, 3, 8, 16))
+    cell = (16.0, 8.0, 1.0)  # dk = 1/16, 1/8
+    # on grid points: exact values, including the periodic wrap
+    kx = np.array([0.0, 3 / 16, -1 / 16, 15 / 16])
+    ky = np.array([0.0, 2 / 8, 0.0, 1 / 8])
+    out = oracle.dispersion(S, cell, kx, ky)
+    want = np.stack([S[0, :, 0, 0], S[0, :, 2, 3], S[0, :, 0, 15], S[0, :, 1, 15]], axis=-1)
+    assert np.allclose(out[0], want)
+    # half-way between two columns: the mean
+    mid = oracle.dispersion(S, cell, np.array([2.5 / 16]), np.array([1 / 8]))
+    assert np.allclose(mid[0, :, 0], 0.5 * (S[0, :, 1, 2] + S[0, :, 1, 3]))
+
+
+def test_defocus_is_free_propagation():
+    # chi = pi lambda df k^2 applied at the aperture equals vacuum propagation over df
+    N, L, df = 64, 16.0, 35.0
+    p = oracle.params(N, N, 1, (L, L, 2.0), bandlimit=0.0)
+    focused = oracle.probe(p, 25.0, 3.0, 5.0)
+    defoc = oracle.probe_aberrated(p, 25.0, 3.0, 5.0, df=df)
+    k = np.fft.fftfreq(N, d=L / N)
+    P = np.exp(-1j * np.pi * oracle.wavelength(100e3) * df * (k[:, None] ** 2 + k[None, :] ** 2))
+    prop = oracle.fft2(P * oracle.fft2(focused, -1), +1) / (N * N)
+    assert np.abs(defoc - prop).max() < 1e-12
+    assert np.abs(oracle.probe_aberrated(p, 25.0, 3.0, 5.0) - focused).max() < 1e-13
+    assert abs(np.sum(np.abs(oracle.probe_aberrated(p, 25.0, cs_mm=1.2, a1=40.0, phi_a=0.3)) ** 2) - 1) < 1e-12
+
+
+def test_multislice_from_initial_waves_matches_probe_path():
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=3)
+    p = oracle.params_of(w)
+    xy = np.array([[1.0, 2.0], [4.5, 0.5]])
+    a = oracle.multislice_frame(p, w.pos[0], w.Z, w.form_Z, w.form_coef, 30.0, xy)
+    psi0 = np.stack([oracle.probe(p, 30.0, *r) for r in xy])
+    b = oracle.multislice_frame_init(p, w.pos[0], w.Z, w.form_Z, w.form_coef, psi0)
+    assert np.abs(a - b).max() < 1e-14
