@@ -49,6 +49,8 @@ def make_workload(name, seed_offset=0, frames=None):
         w = workloads.config3(n_frames=frames or 256, seed=3 + seed_offset)
     elif name == "c4":
         w = workloads.config4(n_frames=frames or 2048, seed=4 + seed_offset)
+    elif name == "m1":
+        w = workloads.minimal_example_si(n_frames=frames or 200, seed=6 + seed_offset)
     else:
         raise SystemExit(f"unknown workload {name}")
     return w
@@ -366,7 +368,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m1"])
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

@@ -262,6 +262,22 @@ def config4(n_frames=2048, grid=1024, seed=4):
                       name=f"c4-diamond-si-{n_frames}x{grid}sq")
 
 
+def minimal_example_si(n_frames=200, grid=1024, n_slices=54, seed=6, n_scan=0):
+    """The shape of the paper's minimal example (Supplement, "Minimal Working Example"):
+    diamond Si a = 5.431 A, 20 x 20 x 5 cells (16,000 atoms, 108.62 x 108.62 x 27.155 A), 200
+    frames 10 fs apart, 100 keV, ~0.1 A sampling (1024^2: 0.106 A), slices of ~0.5 A (54).
+    Thermal-like seeded displacements (32 modes, 0.06 A RMS) stand in for the MLIP MD."""
+    reps = (20, 20, 5)
+    R, Z, cell = diamond(5.431, reps)
+    rng = SplitMix64(seed)
+    modes = random_modes(rng, 32, cell, reps, amp=None)
+    kw = {}
+    if n_scan:
+        kw = dict(alpha_mrad=30.0, probes=probe_grid(cell[0], cell[1], n_scan))
+    return _finish(f"minimal-example-si-{n_frames}x{grid}sq", R, Z, cell, modes, n_frames, 10.0, n_slices, grid,
+                   0.5, rms=0.06, **kw)
+
+
 def single_mode_si(n_frames=32, m0=2, dt_fs=5.0, grid=32, n_slices=4, amp=0.05, q=(1, 0, 0),
                    reps=(1, 1, 1), phase=0.3, eps=(0.0, 0.6, 0.8)):
     """One mode whose frequency sits exactly on DFT bin m0: f = m0 / (F dt)."""
