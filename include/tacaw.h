@@ -249,8 +249,11 @@ int tacaw_serving_stats(tacaw_ctx* ctx, int64_t* queued, int64_t* active, uint64
 int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, float* S_out, void* stream);
 
 /* Context option.  "max_chunk_frames": cap on the frames whose waves are propagated together
- * in one batch of launches (0 = automatic, sized to the L2-resident working set; 1 gives the
- * plain frame-at-a-time path).  EINVAL for an unknown name or a bad value. */
+ * in one batch of launches (0 = automatic: a bounded scratch of 2 GB per chunk; 1 gives the
+ * plain frame-at-a-time path).  "max_slice_block": cap on the slices whose potentials and
+ * transmission functions tacaw_run builds together for a chunk of frames (0 = automatic: all
+ * S slices unless that would leave a slice launch with fewer than 16384 wave rows).  Results
+ * do not depend on either option.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 
 /* Wait for all work on the context's device, then report TACAW_ETIMEOUT if any kernel of the

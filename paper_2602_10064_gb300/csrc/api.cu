@@ -460,11 +460,12 @@ int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, Sc
   return TACAW_OK;
 }
 
-// Potential of frames [0, nf): binning, spreading row pass, column pass.  Leaves Ap (per
-// chunk) to `sink(f0, nfc, Ap)`, which runs the row pass out of the potential.
+// Potential of frames [0, nf): binning, then per chunk of `chunk` frames and per block of `sb`
+// slices the spreading row pass and the column pass.  Leaves Ap [nfc][sbc][ny][Wp] to
+// `sink(f0, nfc, s0, sbc, Ap)`, which runs the row pass out of the potential.
 template <class Sink>
 int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float* pos, const int8_t* slots,
-                     int64_t A, int64_t nf, int64_t chunk, Scratch& sc, Sink sink) {
+                     int64_t A, int64_t nf, int64_t chunk, int sb, Scratch& sc, Sink sink) {
   const int S = p.n_slices, ny = p.ny;
   const Geo geo{p.nx, p.ny, ctx->tw};
   AtomRec* recs;
@@ -477,26 +478,28 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
   }
   float2 *Bp, *Ap;
   const size_t plane = (size_t)ny * g->band.Wp;
-  CK(sc.get(&Bp, (size_t)chunk * S * g->npair * plane));
-  CK(sc.get(&Ap, (size_t)chunk * S * plane));
+  CK(sc.get(&Bp, (size_t)chunk * sb * g->npair * plane));
+  CK(sc.get(&Ap, (size_t)chunk * sb * plane));
   const SpreadKernel sk{kSpreadHalf, (float)kSpreadBeta};
+  const double W8 = (double)g->band.W * 8.0, fx = 5.0 * p.nx * std::log2((double)p.nx),
+               fy = 5.0 * ny * std::log2((double)ny);
   for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
     const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
-    const int nfs = nfc * S;
-    const double W8 = (double)g->band.W * 8.0, fx = 5.0 * p.nx * std::log2((double)p.nx),
-                 fy = 5.0 * ny * std::log2((double)ny);
-    {
-      ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 + (double)nfs * g->npair * ny * W8,
-                   (double)nfs * g->npair * ny * fx);
-      CK(launch_splat_row(geo, g->band, recs + (size_t)f0 * A, offs + (size_t)f0 * (S + 1), A, S, nfs, g->npair,
-                          sk, Bp, sc.st));
+    for (int s0 = 0; s0 < S; s0 += sb) {
+      const int sbc = std::min(sb, S - s0), nfs = nfc * sbc;
+      {
+        ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
+                     (double)nfs * g->npair * ny * fx);
+        CK(launch_splat_row(geo, g->band, recs + (size_t)f0 * A, offs + (size_t)f0 * (S + 1), A, S, s0, sbc, nfs,
+                            g->npair, sk, Bp, sc.st));
+      }
+      {
+        ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
+                     (double)nfs * (g->npair + 1) * g->band.W * fy);
+        CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
+      }
+      TRY_RC(sink(f0, nfc, s0, sbc, Ap));
     }
-    {
-      ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
-                   (double)nfs * (g->npair + 1) * g->band.W * fy);
-      CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
-    }
-    TRY_RC(sink(f0, nfc, Ap));
   }
   return TACAW_OK;
 }
@@ -628,23 +631,26 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
   return TACAW_OK;
 }
 
-// Multislice of nfc frames whose transmission functions are t[fl][s][ny][nx]; exit waves go to
-// psi_k[p][f0 + fl] of a [P][F_total][ny][nx] stack (zeroed by the caller).
-int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, int nfc, int P, const float2* psi0,
-           int64_t F_total, int64_t f0, float2* psi_k, Scratch& sc, float2* Apsi, float2* Bpsi, bool tfused) {
+// Slices [s0, s0 + sb) of the multislice of nfc frames, whose transmission functions are
+// t[fl][s - s0][ny][nx] (or the compact [..][ny][Wp] with `tfused`); the waves carry over in
+// Apsi between calls, and the exit waves go to psi_k[p][f0 + fl] of a [P][F_total][ny][nx]
+// stack (zeroed by the caller) when the block holds the last slice.
+int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, int nfc, int s0, int sb, int P,
+           const float2* psi0, int64_t F_total, int64_t f0, float2* psi_k, Scratch& sc, float2* Apsi, float2* Bpsi,
+           bool tfused) {
   const Geo geo{p.nx, p.ny, ctx->tw};
   const int S = p.n_slices;
   const float nq = (float)p.nx * (float)p.ny;
   const float plane_amp = (float)(1.0 / std::sqrt((double)p.nx * p.ny));
-  for (int s = 0; s < S; ++s) {
+  const double W8 = (double)g->band.W * 8.0, rows = (double)P * nfc * p.ny,
+               fx = 5.0 * p.nx * std::log2((double)p.nx), fy = 5.0 * p.ny * std::log2((double)p.ny);
+  for (int s = s0; s < s0 + sb; ++s) {
     const bool last = s == S - 1;
-    const double W8 = (double)g->band.W * 8.0, rows = (double)P * nfc * p.ny,
-                 fx = 5.0 * p.nx * std::log2((double)p.nx), fy = 5.0 * p.ny * std::log2((double)p.ny);
     {
       const double in = s > 0 ? W8 : (psi0 ? 8.0 * p.nx : 0.0), tin = tfused ? W8 : 8.0 * p.nx;
       ProfScope ps(ctx, "slice_row", sc.st, rows * (in + tin + W8), rows * ((s > 0 ? 2 : 1) + (tfused ? 1 : 0)) * fx);
-      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, tfused, Apsi, psi0, t, S, s, P, nfc, plane_amp,
-                          Bpsi, sc.st));
+      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, tfused, Apsi, psi0, t, sb, s - s0, P, nfc,
+                          plane_amp, Bpsi, sc.st));
     }
     {
       ProfScope ps(ctx, "slice_col", sc.st, rows * 2 * W8, (double)P * nfc * g->band.W * (last ? 1 : 2) * fy);
@@ -678,13 +684,30 @@ int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr,
   return TACAW_OK;
 }
 
-// Frames per chunk of a run (bounded scratch; intermediates of a chunk stay near L2).
-int64_t run_chunk(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t F) {
-  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
-  const size_t S = (size_t)p.n_slices;
-  const size_t per_frame = S * nq * 8 + S * plane * 8 * (g->npair + 3) + (size_t)P * plane * 16;
-  const int64_t c = chunk_frames(F, per_frame, (size_t)2 << 30);
-  return ctx->max_chunk_frames > 0 ? std::min<int64_t>(c, ctx->max_chunk_frames) : c;
+// Tiling of a run: frames per chunk and slices per block.  A chunk's scratch stays under
+// 2 GB; the slice block shrinks below S only when that is what lets one slice launch hold at
+// least kMinWaveRows wave rows (several waves of CTAs on every SM), so that the number of
+// waves per launch does not fall with the slice count or the grid size.
+constexpr int64_t kMinWaveRows = 16384;
+struct RunTiling {
+  int64_t chunk;
+  int sb;
+};
+RunTiling run_tiling(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t F) {
+  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp, cap = (size_t)2 << 30;
+  const int S = p.n_slices;
+  const size_t per_slice = nq * 8 + plane * 8 * (g->npair + 3), wave = (size_t)P * plane * 16;
+  int64_t want = std::min<int64_t>(F, (kMinWaveRows + (int64_t)P * p.ny - 1) / ((int64_t)P * p.ny));
+  if (ctx->max_chunk_frames > 0) want = std::min<int64_t>(want, ctx->max_chunk_frames);
+  int sb = S;
+  if ((size_t)want * (S * per_slice + wave) > cap) {
+    const size_t room = cap / (size_t)want;
+    sb = room > wave ? (int)std::min<size_t>(S, std::max<size_t>(1, (room - wave) / per_slice)) : 1;
+  }
+  if (ctx->max_slice_block > 0) sb = (int)std::min<int64_t>(sb, ctx->max_slice_block);
+  int64_t c = chunk_frames(F, sb * per_slice + wave, cap);
+  if (ctx->max_chunk_frames > 0) c = std::min<int64_t>(c, ctx->max_chunk_frames);
+  return RunTiling{c, sb};
 }
 
 // Device bytes a run allocates from the stream-ordered pool (tables cached in the context
@@ -692,11 +715,12 @@ int64_t run_chunk(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g
 uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
                        int32_t reduce, GeoCache* g) {
   const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
-  const int64_t chunk = run_chunk(ctx, p, g, P, F);
+  const RunTiling rt = run_tiling(ctx, p, g, P, F);
+  const double chunk = (double)rt.chunk, sb = rt.sb;
   double b = 0;
   b += (double)F * A * (12 + 16) + (double)F * (S + 1) * 4 + A;     // positions, records, offsets, slots
-  b += chunk * S * plane * 8 * (g->npair + 2);                       // Bp, Ap, Bt
-  b += chunk * S * nq * 8;                                            // t (or At)
+  b += chunk * sb * plane * 8 * (g->npair + 2);                      // Bp, Ap, Bt
+  b += chunk * sb * nq * 8;                                           // t (or At)
   b += chunk * (double)P * plane * 16;                                // Apsi, Bpsi
   b += (double)P * nq * 16;                                           // probes
   b += (double)P * F * nq * 8;                                        // exit waves
@@ -728,17 +752,18 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
   float2* psi_k;
   CK(sc.get(&psi_k, (size_t)P * F * nq));
   CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
-  const int64_t chunk = run_chunk(ctx, p, g, P, F);
+  const RunTiling rt = run_tiling(ctx, p, g, P, F);
   float2 *t, *Apsi, *Bpsi;
-  CK(sc.get(&t, (size_t)chunk * S * nq));
-  CK(sc.get(&Apsi, (size_t)chunk * P * plane));
-  CK(sc.get(&Bpsi, (size_t)chunk * P * plane));
+  CK(sc.get(&t, (size_t)rt.chunk * rt.sb * nq));
+  CK(sc.get(&Apsi, (size_t)rt.chunk * P * plane));
+  CK(sc.get(&Bpsi, (size_t)rt.chunk * P * plane));
   const bool tf = use_compact_t(p, P);
   TransBufs tb;
-  TRY_RC(trans_bufs(ctx, p, g, chunk * S, tf, sc, &tb));
-  TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
-    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * S, t, sc, tb, tf));
-    return slices(ctx, p, g, t, nfc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
+  TRY_RC(trans_bufs(ctx, p, g, rt.chunk * rt.sb, tf, sc, &tb));
+  TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, rt.chunk, rt.sb, sc,
+                          [&](int64_t f0, int nfc, int s0, int sbc, float2* Ap) {
+    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * sbc, t, sc, tb, tf));
+    return slices(ctx, p, g, t, nfc, s0, sbc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
   }));
   return spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc);
 }
@@ -786,7 +811,8 @@ int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const floa
   const Geo geo{p.nx, p.ny, ctx->tw};
   const size_t plane = (size_t)p.ny * g->band.Wp;
   const int64_t chunk = chunk_frames(nf, p.n_slices * plane * 8 * (g->npair + 1), (size_t)1 << 30);
-  return potential_chunks(ctx, p, g, pos, slots, n_atoms, nf, chunk, sc, [&](int64_t f0, int nfc, float2* Ap) {
+  return potential_chunks(ctx, p, g, pos, slots, n_atoms, nf, chunk, p.n_slices, sc,
+                          [&](int64_t f0, int nfc, int, int, float2* Ap) {
     CK(launch_row_pot_out(geo, g->band, Ap, nfc * p.n_slices, 0, 0.f,
                           V_out + (size_t)f0 * p.n_slices * p.ny * p.nx, nullptr, st));
     return TACAW_OK;
@@ -852,7 +878,7 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
   for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
     const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
     TRY_RC(transmission_from(ctx, p, g, nullptr, V + (size_t)f0 * S * nq, nfc * S, t, sc, tb, tf));
-    TRY_RC(slices(ctx, p, g, t, nfc, P, psi0, nf, f0, psi_k, sc, Apsi, Bpsi, tf));
+    TRY_RC(slices(ctx, p, g, t, nfc, 0, S, P, psi0, nf, f0, psi_k, sc, Apsi, Bpsi, tf));
   }
   return TACAW_OK;
 }
@@ -912,6 +938,11 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (std::strcmp(name, "max_chunk_frames") == 0) {
     if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_chunk_frames must be >= 0");
     ctx->max_chunk_frames = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "max_slice_block") == 0) {
+    if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_slice_block must be >= 0");
+    ctx->max_slice_block = value;
     return TACAW_OK;
   }
   return set_err(ctx, TACAW_EINVAL, "unknown option '%s'", name);

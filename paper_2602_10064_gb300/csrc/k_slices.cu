@@ -206,7 +206,7 @@ struct SplatSmem {
 template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
-                int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
+                int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 
   const int bidx = batch_index();
   if (bidx >= nbatch) return;
-  const int pair = bidx % npair, fs = bidx / npair, f = fs / S, s = fs % S;
+  const int pair = bidx % npair, fs = bidx / npair, f = fs / sb, s = s0 + fs % sb;
   const int tid = threadIdx.x, g = tid / T, t = tid % T, lane = tid & 31, w = tid >> 5;
   const int ny = geo.ny, y0 = blockIdx.x * G;
   const int h = sk.half, W2 = 2 * h;
@@ -659,19 +659,21 @@ static cudaError_t prep(K kernel, int smem) {
 
 template <int NX>
 static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A,
-                               int S, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
+                               int S, int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp,
+                               cudaStream_t st) {
+  if (s0 < 0 || sb < 1 || s0 + sb > S || nfs % sb != 0) return cudaErrorInvalidValue;
   if (2 * sk.half > SPREAD_MAX_W) return cudaErrorInvalidValue;
   const int smem = SplatSmem<NX>::BYTES;
   cudaError_t e = prep(k_splat_row<NX>, smem);
   if (e != cudaSuccess) return e;
   const int nb = nfs * npair;
   k_splat_row<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nb), RowCfg<NX>::THREADS, smem, st>>>(
-      g, b, recs, offs, (int)A, S, npair, nb, sk, Bp);
+      g, b, recs, offs, (int)A, S, s0, sb, npair, nb, sk, Bp);
   return cudaGetLastError();
 }
 cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A, int S,
-                             int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
-  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, offs, A, S, nfs, npair, sk, Bp, st);
+                             int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, offs, A, S, s0, sb, nfs, npair, sk, Bp, st);
 }
 
 template <int NY>

@@ -61,6 +61,7 @@ struct tacaw_ctx {
   std::map<int64_t, std::pair<void*, void*>> dft_ops;  // tensor-core DFT operands (hi, lo) per F and kind
   int* d_status = nullptr;  // device status word: nonzero after a kernel's bounded wait ran out
   int64_t max_chunk_frames = 0;  // option: cap on frames per chunk (0 = automatic)
+  int64_t max_slice_block = 0;   // option: cap on slices per block of a run (0 = automatic)
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };

@@ -46,8 +46,9 @@ struct SpreadKernel {
 cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
                        int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
                        cudaStream_t st);
+// Spreading row pass of slices [s0, s0 + sb) of nfs / sb frames (batch = (frame, slice, pair)).
 cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A, int S,
-                             int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st);
+                             int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st);
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                            float2* Ap, cudaStream_t st);
 // mode 0: store V; mode 1: t = exp(i sigma V), band-limit pass input (FFT_x, compact);

@@ -315,6 +315,37 @@ def test_run_is_deterministic(ctx, T):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("probe", [False, True])
+def test_run_tiling_does_not_change_result(ctx, T, probe):
+    """Frame chunks and slice blocks only regroup independent (frame, slice) work and carry the
+    waves across blocks, so every tiling gives the same bits; one of them is held to the oracle."""
+    w = small_rocksalt(n_frames=5, grid=64, S=7, seed=45)
+    if probe:
+        w.alpha_mrad, w.probes = 25.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p, pr = T.params_of(w), T.probe_of(w)
+    pos, Z = dev(w.pos), dev(w.Z)
+    base = ctx.run(p, pos, Z, pr).cpu().numpy()
+    try:
+        for chunk, block in [(0, 1), (0, 3), (2, 2), (3, 5), (1, 7), (4, 6)]:
+            ctx.set_option("max_chunk_frames", chunk)
+            ctx.set_option("max_slice_block", block)
+            got = ctx.run(p, pos, Z, pr).cpu().numpy()
+            assert np.array_equal(got, base), (chunk, block)
+    finally:
+        ctx.set_option("max_chunk_frames", 0)
+        ctx.set_option("max_slice_block", 0)
+    want = oracle.tacaw(w)
+    assert rel(base, want) < TOL_S, rel(base, want)
+
+
+def test_set_option_rejects_bad_values(ctx, T):
+    with pytest.raises(T.TacawError):
+        ctx.set_option("max_slice_block", -1)
+    with pytest.raises(T.TacawError):
+        ctx.set_option("no_such_option", 1)
+
+
 # ------------------------------------------------------------------------------------------
 # full-size configuration 2 (512^2, 8000 atoms, 20 slices): sampled frames
 # ------------------------------------------------------------------------------------------
