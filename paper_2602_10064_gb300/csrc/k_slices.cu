@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 }
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
-template <int NY>
+template <int NY, bool ONE>
 __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
@@ -318,6 +318,22 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
   const ColIdx<C> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + NY;
+  if (ONE) {
+    // one species pair: no accumulator held across the transforms
+    const float2* src = Bp + (size_t)fs * NY * b.Wp + cc;
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+    fft<NY, -1>(v, sm, idx, t, tw, sync);
+    const float2* m = mtab + cc;
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
+    fft<NY, +1>(v, sm, idx, t, tw, sync);
+    float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
+#pragma unroll
+    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
+    return;
+  }
   float2 acc[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = make_float2(0.f, 0.f);
@@ -679,8 +695,11 @@ cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, c
 template <int NY>
 static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                              float2* Ap, cudaStream_t st) {
-  k_col_pot<NY><<<batch_grid(b.Wp / ColCfg<NY>::C, nfs), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(
-      g, b, Bp, mtab, npair, nfs, Ap);
+  const dim3 grid = batch_grid(b.Wp / ColCfg<NY>::C, nfs);
+  if (npair == 1)
+    k_col_pot<NY, true><<<grid, ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
+  else
+    k_col_pot<NY, false><<<grid, ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
   return cudaGetLastError();
 }
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
