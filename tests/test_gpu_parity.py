@@ -81,10 +81,20 @@ def test_bin_slices_bit_exact(ctx, T):
 # ------------------------------------------------------------------------------------------
 # a2 projected potential
 # ------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_half"])
+def three_species():
+    """Rocksalt with every third atom made Si: three species, so two species pairs are spread."""
+    w = small_rocksalt(n_frames=2)
+    w.Z = w.Z.copy()
+    w.Z[::3] = 14
+    w.form_Z, w.form_coef = workloads.placeholder_form_factors(w.Z)
+    return w
+
+
+@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_half", "three_species"])
 def test_potential_parity(ctx, T, case):
     w = {"c1": lambda: workloads.diamond_si(n_frames=2), "rocksalt": small_rocksalt, "rect": rect_diamond,
-         "bl_half": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4)}[case]()
+         "bl_half": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4),
+         "three_species": three_species}[case]()
     kw = {"bandlimit": 0.5} if case == "bl_half" else {}
     ctx.load_form_factors(w.form_Z, w.form_coef)
     p = T.params_of(w, **kw)
