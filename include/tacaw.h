@@ -252,8 +252,9 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * in one batch of launches (0 = automatic: a bounded scratch of 2 GB per chunk; 1 gives the
  * plain frame-at-a-time path).  "max_slice_block": cap on the slices whose potentials and
  * transmission functions tacaw_run builds together for a chunk of frames (0 = automatic: all
- * S slices unless that would leave a slice launch with fewer than 16384 wave rows).  Results
- * do not depend on either option.  EINVAL for an unknown name or a bad value. */
+ * S slices unless that would leave a slice launch with fewer than "min_wave_rows" wave rows,
+ * default 65536).  Results do not depend on these options.  EINVAL for an unknown name or a
+ * bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 
 /* Wait for all work on the context's device, then report TACAW_ETIMEOUT if any kernel of the

@@ -688,7 +688,7 @@ int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr,
 // 2 GB; the slice block shrinks below S only when that is what lets one slice launch hold at
 // least kMinWaveRows wave rows (several waves of CTAs on every SM), so that the number of
 // waves per launch does not fall with the slice count or the grid size.
-constexpr int64_t kMinWaveRows = 16384;
+constexpr int64_t kMinWaveRows = 65536;  // default of the "min_wave_rows" option
 struct RunTiling {
   int64_t chunk;
   int sb;
@@ -697,7 +697,8 @@ RunTiling run_tiling(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache
   const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp, cap = (size_t)2 << 30;
   const int S = p.n_slices;
   const size_t per_slice = nq * 8 + plane * 8 * (g->npair + 3), wave = (size_t)P * plane * 16;
-  int64_t want = std::min<int64_t>(F, (kMinWaveRows + (int64_t)P * p.ny - 1) / ((int64_t)P * p.ny));
+  const int64_t rows = ctx->min_wave_rows > 0 ? ctx->min_wave_rows : kMinWaveRows;
+  int64_t want = std::min<int64_t>(F, (rows + (int64_t)P * p.ny - 1) / ((int64_t)P * p.ny));
   if (ctx->max_chunk_frames > 0) want = std::min<int64_t>(want, ctx->max_chunk_frames);
   int sb = S;
   if ((size_t)want * (S * per_slice + wave) > cap) {
@@ -938,6 +939,11 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (std::strcmp(name, "max_chunk_frames") == 0) {
     if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_chunk_frames must be >= 0");
     ctx->max_chunk_frames = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "min_wave_rows") == 0) {
+    if (value < 0) return set_err(ctx, TACAW_EINVAL, "min_wave_rows must be >= 0");
+    ctx->min_wave_rows = value;
     return TACAW_OK;
   }
   if (std::strcmp(name, "max_slice_block") == 0) {

@@ -62,6 +62,7 @@ struct tacaw_ctx {
   int* d_status = nullptr;  // device status word: nonzero after a kernel's bounded wait ran out
   int64_t max_chunk_frames = 0;  // option: cap on frames per chunk (0 = automatic)
   int64_t max_slice_block = 0;   // option: cap on slices per block of a run (0 = automatic)
+  int64_t min_wave_rows = 0;     // option: wave rows a slice launch should hold (0 = default)
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };

@@ -337,14 +337,17 @@ def test_run_tiling_does_not_change_result(ctx, T, probe):
     pos, Z = dev(w.pos), dev(w.Z)
     base = ctx.run(p, pos, Z, pr).cpu().numpy()
     try:
-        for chunk, block in [(0, 1), (0, 3), (2, 2), (3, 5), (1, 7), (4, 6)]:
+        for chunk, block, rows in [(0, 1, 0), (0, 3, 0), (2, 2, 0), (3, 5, 0), (1, 7, 0), (4, 6, 0), (0, 0, 64),
+                                   (0, 0, 1 << 20)]:
             ctx.set_option("max_chunk_frames", chunk)
             ctx.set_option("max_slice_block", block)
+            ctx.set_option("min_wave_rows", rows)
             got = ctx.run(p, pos, Z, pr).cpu().numpy()
             assert np.array_equal(got, base), (chunk, block)
     finally:
         ctx.set_option("max_chunk_frames", 0)
         ctx.set_option("max_slice_block", 0)
+        ctx.set_option("min_wave_rows", 0)
     want = oracle.tacaw(w)
     assert rel(base, want) < TOL_S, rel(base, want)
 
@@ -352,6 +355,8 @@ def test_run_tiling_does_not_change_result(ctx, T, probe):
 def test_set_option_rejects_bad_values(ctx, T):
     with pytest.raises(T.TacawError):
         ctx.set_option("max_slice_block", -1)
+    with pytest.raises(T.TacawError):
+        ctx.set_option("min_wave_rows", -1)
     with pytest.raises(T.TacawError):
         ctx.set_option("no_such_option", 1)
 
