@@ -233,7 +233,9 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[E], float2* sm, const Idx& 
 // SIGN = -1 forward, +1 inverse.  All T threads of the group call it together; sm (through
 // idx) is the group's private scratch; sync is the barrier of the threads sharing it.  tw
 // points at the table for length N.
-template <int N, int SIGN, int E, class Idx, class Sync>
+// PLAN selects the radix schedule where there is a choice: 0 = radix-16 passes, 1 = radix-8
+// passes (two butterflies per thread and pass) for 512 and 1024 points with E = 16.
+template <int N, int SIGN, int PLAN = 0, int E, class Idx, class Sync>
 __device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const Idx& idx, int t,
                                     const float2* __restrict__ tw, const Sync& sync) {
   if constexpr (N == 32) {
@@ -265,6 +267,14 @@ __device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const Idx& idx, 
   } else if constexpr (N == 256) {
     fft_pass<256, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<256, E, 16, 16, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (PLAN == 1 && N == 512) {
+    fft_pass<512, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 8, 64, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (PLAN == 1 && N == 1024) {
+    fft_pass<1024, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 8, 8, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 16, 64, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (N == 512) {
     fft_pass<512, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<512, E, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);

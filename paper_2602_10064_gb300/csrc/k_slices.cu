@@ -17,10 +17,27 @@
 
 namespace tacaw {
 
-// Minimum resident CTAs per SM requested from the compiler for the FFT pass kernels.
-#ifndef TACAW_FFT_MINB
-#define TACAW_FFT_MINB 2
+// Per-kernel variants of the FFT pass kernels, chosen per transform length by the autotuner
+// (paper_2602_10064_gb300/tune.py), which times every variant on GB300 and writes
+// tuning_table.h.  Variant bits: 1 = radix-8 plans (512 and 1024 points), 2 = three resident
+// CTAs per SM (register cap 80) instead of two (128).  TACAW_TUNE_FORCE=v builds every kernel
+// as variant v (the tuner's measurement builds).
+enum KernelId {
+  K_SPLAT_ROW, K_COL_POT, K_ROW_POT_OUT, K_ROW_VT, K_COL_T, K_ROW_TOUT, K_PROBE_COL, K_PROBE_ROW,
+  K_SLICE_ROW, K_SLICE_COL
+};
+}  // namespace tacaw
+#include "tuning_table.h"
+namespace tacaw {
+#ifndef TACAW_TUNE_FORCE
+#define TACAW_TUNE_FORCE -1
 #endif
+template <int K, int N>
+struct Tuned {
+  static constexpr int V = TACAW_TUNE_FORCE >= 0 ? TACAW_TUNE_FORCE : tuned_variant(K, N);
+  static constexpr int PLAN = V & 1;
+  static constexpr int MINB = (V & 2) ? 3 : 2;
+};
 
 // Elements per thread of the row and of the column transforms (8 or 16).
 #ifndef TACAW_ROW_E
@@ -204,10 +221,11 @@ struct SplatSmem {
 };
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::MINB)
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
                 int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
+  constexpr int PL = Tuned<K_SPLAT_ROW, NX>::PLAN;
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);                     // FFT scratch (after spreading)
@@ -300,16 +318,17 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = acc[g * NX + t + T * e];
   __syncthreads();  // the FFT scratch of one group overlaps the accumulators of the next
-  fft<NX, -1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   store_row_compact<NX>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
 }
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
 template <int NY, bool ONE>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_COL_POT, NY>::MINB)
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
   constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  constexpr int PL = Tuned<K_COL_POT, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -324,11 +343,11 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     float2 v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-    fft<NY, -1>(v, sm, idx, t, tw, sync);
+    fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
     const float2* m = mtab + cc;
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
-    fft<NY, +1>(v, sm, idx, t, tw, sync);
+    fft<NY, +1, PL>(v, sm, idx, t, tw, sync);
     float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
 #pragma unroll
     for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
@@ -342,12 +361,12 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     float2 v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-    fft<NY, -1>(v, sm, idx, t, tw, sync);
+    fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
     const float2* m = mtab + (size_t)pr * NY * b.Wp + cc;
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
   }
-  fft<NY, +1>(acc, sm, idx, t, tw, sync);
+  fft<NY, +1, PL>(acc, sm, idx, t, tw, sync);
   float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = acc[e];
@@ -356,10 +375,11 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
 // Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
 // t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>::MINB)
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int PL = Tuned<K_ROW_POT_OUT, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -369,7 +389,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
   const auto sync = group_sync<T>(g);
   float2 v[E];
   load_row_compact<NX>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
+  fft<NX, +1, PL>(v, sm, idx, t, geo.tw + NX, sync);
   const size_t row = ((size_t)fs * ny + y) * NX;
   if (mode == 0) {
 #pragma unroll
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1>(v, sm, idx, t, geo.tw + NX, sync);
+  fft<NX, -1, PL>(v, sm, idx, t, geo.tw + NX, sync);
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
@@ -395,10 +415,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 // a3: transmission from a stored V.
 // ============================================================================================
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::MINB)
     k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
              float2* __restrict__ out) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int PL = Tuned<K_ROW_VT, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -417,15 +438,16 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_COL_T, NY>::MINB)
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
   constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  constexpr int PL = Tuned<K_COL_T, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -438,14 +460,14 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-  fft<NY, -1>(v, sm, idx, t, tw, sync);
+  fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
   const int nb = cc < b.W ? b.colnb[cc] : -1;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int n = fftfreq_index(t + T * e, NY);
     v[e] = (abs(n) <= nb) ? scale * v[e] : make_float2(0.f, 0.f);
   }
-  fft<NY, +1>(v, sm, idx, t, tw, sync);
+  fft<NY, +1, PL>(v, sm, idx, t, tw, sync);
   float2* dst = At + (size_t)fs * NY * b.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
@@ -453,9 +475,10 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
 
 // Row pass out of the band limit: IFFT_x -> t (full row).
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::MINB)
     k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int PL = Tuned<K_ROW_TOUT, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
@@ -463,7 +486,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, At + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   float2* dst = tout + ((size_t)fs * ny + y) * NX;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[t + T * e] = v[e];
@@ -473,10 +496,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
 // Probe: psi0(k) = A(k) exp(-2 pi i k.r_p) amp, then a unitary inverse transform.
 // ============================================================================================
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_PROBE_COL, NY>::MINB)
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey,
                 const float2* __restrict__ chi, int P, float amp, float2* __restrict__ Bpr) {
   constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  constexpr int PL = Tuned<K_PROBE_COL, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int p = batch_index();
@@ -491,16 +515,17 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     v[e] = (abs(n) <= nb) ? amp * cmul(exv, ey[(size_t)p * NY + row]) : make_float2(0.f, 0.f);
     if (chi && abs(n) <= nb) v[e] = cmul(v[e], chi[(size_t)row * ap.Wp + cc]);
   }
-  fft<NY, +1>(v, sm, ColIdx<C>{c}, t, geo.tw + NY, BlockSync{});
+  fft<NY, +1, PL>(v, sm, ColIdx<C>{c}, t, geo.tw + NY, BlockSync{});
   float2* dst = Bpr + (size_t)p * NY * ap.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * ap.Wp] = v[e];
 }
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_PROBE_ROW, NX>::MINB)
     k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int PL = Tuned<K_PROBE_ROW, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int p = batch_index();
@@ -508,7 +533,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, Bpr + ((size_t)p * ny + y) * ap.Wp, ap, t);
-  fft<NX, +1>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
   float2* dst = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[t + T * e] = scale * v[e];
@@ -526,11 +551,12 @@ struct SliceRowSmem {
 };
 
 template <int NX, bool FIRST, bool PLANE, bool TF>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::MINB)
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
                 float2* __restrict__ Bpsi) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int PL = Tuned<K_SLICE_ROW, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int w = batch_index();
@@ -553,7 +579,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
   float2* tst = reinterpret_cast<float2*>(smraw + RowCfg<NX>::SMEM) + g * NX;
   if (TF) {
     load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
-    fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
+    fft<NX, +1, PL>(v, sm, idx, t, geo.tw + NX, sync);
 #pragma unroll
     for (int e = 0; e < E; ++e) tst[t + T * e] = v[e];
   }
@@ -569,20 +595,21 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, TACAW_FFT_MINB)
     }
   } else {
     load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
-    fft<NX, +1>(v, sm, idx, t, geo.tw + NX, sync);
+    fft<NX, +1, PL>(v, sm, idx, t, geo.tw + NX, sync);
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmul(v[e], TF ? tst[t + T * e] : trow[t + T * e]);
   }
-  fft<NX, -1>(v, sm, idx, t, geo.tw + NX, sync);
+  fft<NX, -1, PL>(v, sm, idx, t, geo.tw + NX, sync);
   store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
 }
 
 template <int NY, bool LAST>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
+__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_SLICE_COL, NY>::MINB)
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
   constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  constexpr int PL = Tuned<K_SLICE_COL, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int w = batch_index();
@@ -595,7 +622,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-  fft<NY, -1>(v, sm, idx, t, tw, sync);
+  fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
   const int nb = cc < b.W ? b.colnb[cc] : -1;
   const float2 pxc = cc < b.W ? px[cc] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -613,7 +640,7 @@ __global__ void __launch_bounds__(ColCfg<NY>::THREADS, TACAW_FFT_MINB)
     }
     return;
   }
-  fft<NY, +1>(v, sm, idx, t, tw, sync);
+  fft<NY, +1, PL>(v, sm, idx, t, tw, sync);
   float2* dst = Apsi + (size_t)w * NY * b.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
