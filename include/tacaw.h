@@ -105,7 +105,8 @@ const char* tacaw_last_error(const tacaw_ctx* ctx);
 /* Load form-factor coefficients (Methods, "Atomic Scattering Potentials": Kirkland's form
  * f(q) = sum_i a_i/(q^2+b_i) + c_i exp(-d_i q^2), q in 1/A without 2 pi, f in A).
  * Z: HOST [nZ] atomic numbers; coef: HOST [nZ][12] as a1 b1 a2 b2 a3 b3 c1 d1 c2 d2 c3 d3.
- * Replaces any earlier table.  EINVAL for nZ < 1, nZ > 64, repeated Z or b_i <= 0. */
+ * Replaces any earlier table.  EINVAL for nZ < 1, nZ > 64, Z outside [1, 255], repeated Z
+ * or b_i <= 0. */
 int tacaw_load_form_factors(tacaw_ctx* ctx, const int32_t* Z, const double* coef, int32_t nZ);
 
 /* Slice binning (Methods, "Atomic Scattering Potentials": the sum runs over the atoms inside
@@ -152,7 +153,10 @@ int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int
  * pos: float32 [F][n_atoms][3] and Z: int32 [n_atoms], HOST or DEVICE; S_out: float32
  * [P][F][ny][nx] (REDUCE_NONE) or [P][F] (REDUCE_DETECTOR), HOST or DEVICE.  With host
  * buffers the copies are part of the call (pinned host memory is fastest).  Synchronous on
- * `stream` when any buffer is on the host, asynchronous otherwise. */
+ * `stream` when any buffer is on the host, asynchronous otherwise.  Z on the device is mapped
+ * to form-factor slots on the device: an atom whose Z is not in the loaded table makes the
+ * next tacaw_check return TACAW_EINVAL (the results of that call are invalid); Z on the host
+ * is checked here (TACAW_EINVAL). */
 int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z, int64_t n_atoms,
               int64_t n_frames, const tacaw_probe* probe, int32_t precision, int32_t reduce, float* S_out,
               void* stream);
@@ -257,9 +261,10 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 
-/* Wait for all work on the context's device, then report TACAW_ETIMEOUT if any kernel of the
- * context gave up a bounded wait since the last check (its outputs are then invalid), else
- * TACAW_OK.  The status is cleared by the check. */
+/* Wait for all work on the context's device, then report what the context's kernels flagged
+ * since the last check: TACAW_ETIMEOUT if a kernel gave up a bounded wait, TACAW_EINVAL if
+ * tacaw_run met a device-resident Z that is not in the form-factor table (the outputs of
+ * those calls are invalid), else TACAW_OK.  The status is cleared by the check. */
 int tacaw_check(tacaw_ctx* ctx);
 
 /* Diagnostics.  tacaw_profile_begin starts recording a CUDA event pair around every kernel

@@ -390,7 +390,8 @@ int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
     }
   if (owned_alloc(ctx, &ctx->tw, tw.size()) != TACAW_OK ||
       cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      owned_alloc(ctx, &ctx->d_status, 1) != TACAW_OK || cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+      owned_alloc(ctx, &ctx->d_status, 1) != TACAW_OK || cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
+      owned_alloc(ctx, &ctx->d_zslot, 256) != TACAW_OK || cudaMemset(ctx->d_zslot, 0xff, 256) != cudaSuccess) {
     for (void* p : ctx->owned) cudaFree(p);
     delete ctx;
     return TACAW_ECUDA;
@@ -423,6 +424,12 @@ int tacaw_load_form_factors(tacaw_ctx* ctx, const int32_t* Z, const double* coef
     for (int k = 0; k < 12; ++k)
       if (!std::isfinite(coef[12 * i + k])) return set_err(ctx, TACAW_EINVAL, "non-finite coefficient");
   }
+  for (int i = 0; i < nZ; ++i)
+    if (Z[i] < 1 || Z[i] > 255) return set_err(ctx, TACAW_EINVAL, "Z=%d outside [1, 255]", Z[i]);
+  std::vector<int8_t> lut(256, -1);
+  for (int i = 0; i < nZ; ++i) lut[Z[i]] = (int8_t)i;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpy(ctx->d_zslot, lut.data(), 256, cudaMemcpyHostToDevice));
   ctx->ffZ.assign(Z, Z + nZ);
   ctx->ffcoef.assign(coef, coef + 12 * (size_t)nZ);
   ctx->ff_version++;
@@ -434,7 +441,16 @@ int tacaw_load_form_factors(tacaw_ctx* ctx, const int32_t* Z, const double* coef
 namespace tacaw {
 
 // Slot (form-factor table index) of every atom; host Z in, device int8 out.
-int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, Scratch& sc, int8_t** d_slot) {
+// Form-factor slot of every atom.  Z on the device with device_check: mapped on the device, an
+// unknown species reported through the status word (tacaw_check), so the host never waits
+// for the stream.  Otherwise Z is checked on the host and an unknown species is EINVAL here.
+int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, bool device_check, Scratch& sc,
+               int8_t** d_slot) {
+  if (z_on_device && device_check) {
+    CK(sc.get(d_slot, std::max<int64_t>(A, 1)));
+    CK(launch_map_slots(Z, A, ctx->d_zslot, *d_slot, ctx->d_status, sc.st));
+    return TACAW_OK;
+  }
   std::vector<int32_t> hz(A);
   if (A > 0) {
     if (z_on_device) {
@@ -454,8 +470,8 @@ int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, Sc
   }
   CK(sc.get(d_slot, A));
   if (A > 0) {
+    // from pageable memory: the call returns once hs is staged, so hs may go out of scope
     CK(cudaMemcpyAsync(*d_slot, hs.data(), A, cudaMemcpyHostToDevice, sc.st));
-    CK(cudaStreamSynchronize(sc.st));  // hs is pageable and local
   }
   return TACAW_OK;
 }
@@ -627,7 +643,6 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
   const Geo geo{nx, ny, ctx->tw};
   CK(launch_probe_col(geo, ap, d_ex, d_ey, d_chi, P, (float)(1.0 / std::sqrt((double)count)), Bpr, sc.st));
   CK(launch_probe_row(geo, ap, Bpr, P, (float)(1.0 / std::sqrt((double)nx * ny)), *psi0, sc.st));
-  CK(cudaStreamSynchronize(sc.st));  // host tables are local
   return TACAW_OK;
 }
 
@@ -746,7 +761,7 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
   const int P = pr.n_probes, S = p.n_slices;
   const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
   int8_t* slots;
-  TRY_RC(make_slots(ctx, Z, A, z_dev, sc, &slots));
+  TRY_RC(make_slots(ctx, Z, A, z_dev, true, sc, &slots));
   float2* psi0 = nullptr;
   if (pr.psi0) psi0 = const_cast<float2*>(reinterpret_cast<const float2*>(pr.psi0));
   else if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
@@ -808,7 +823,7 @@ int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const floa
   TRY_RC(get_geo(ctx, p, &g));
   Scratch sc(st);
   int8_t* slots;
-  TRY_RC(make_slots(ctx, Z, n_atoms, true, sc, &slots));
+  TRY_RC(make_slots(ctx, Z, n_atoms, true, false, sc, &slots));
   const Geo geo{p.nx, p.ny, ctx->tw};
   const size_t plane = (size_t)p.ny * g->band.Wp;
   const int64_t chunk = chunk_frames(nf, p.n_slices * plane * 8 * (g->npair + 1), (size_t)1 << 30);
@@ -963,7 +978,11 @@ int tacaw_check(tacaw_ctx* ctx) {
   CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != 0) {
     CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
-    return set_err(ctx, TACAW_ETIMEOUT, "a kernel's bounded wait ran out (status %d); its results are invalid", st);
+    if (st & TACAW_STATUS_TIMEOUT)
+      return set_err(ctx, TACAW_ETIMEOUT, "a kernel's bounded wait ran out (status %d); its results are invalid", st);
+    return set_err(ctx, TACAW_EINVAL,
+                   "an atom's Z was not in the form-factor table (Z on the device); the results of that run are "
+                   "invalid");
   }
   return TACAW_OK;
 }

@@ -43,8 +43,8 @@ constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*alignment*/ + 256 /*
 constexpr int TC_TMEM_COLS = 2 * TC_BN;  // two accumulator buffers
 constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 
-// status word codes
-constexpr int TC_ERR_TIMEOUT = 1;
+// status word bit of a wait that ran out
+constexpr int TC_ERR_TIMEOUT = TACAW_STATUS_TIMEOUT;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,7 +78,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
   const unsigned long long t0 = globaltimer();
   while (!mbar_try(bar, parity)) {
     if (globaltimer() - t0 > TC_TIMEOUT_NS) {
-      atomicExch(status, TC_ERR_TIMEOUT);
+      atomicOr(status, TC_ERR_TIMEOUT);
       return false;
     }
   }

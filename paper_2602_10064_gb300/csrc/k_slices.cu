@@ -190,6 +190,27 @@ __global__ void __launch_bounds__(BIN_THREADS) k_bin(const float* __restrict__ p
   }
 }
 
+__global__ void k_map_slots(const int32_t* __restrict__ Z, int64_t A, const int8_t* __restrict__ lut,
+                            int8_t* __restrict__ slot, int* __restrict__ status) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < A; j += (int64_t)gridDim.x * blockDim.x) {
+    const int z = Z[j];
+    int s = (z >= 0 && z < 256) ? lut[z] : -1;
+    if (s < 0) {
+      atomicOr(status, TACAW_STATUS_SPECIES);
+      s = 0;
+    }
+    slot[j] = (int8_t)s;
+  }
+}
+
+cudaError_t launch_map_slots(const int32_t* Z, int64_t A, const int8_t* lut, int8_t* slot, int* status,
+                             cudaStream_t st) {
+  if (A <= 0) return cudaSuccess;
+  const int64_t blocks = (A + 255) / 256;
+  k_map_slots<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(Z, A, lut, slot, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
                        int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
                        cudaStream_t st) {

@@ -54,12 +54,12 @@ struct tacaw_ctx {
   float2* tw = nullptr;  // FFT twiddles: length-N table at tw + N (N = 2 .. 2048)
   std::vector<int32_t> ffZ;
   std::vector<double> ffcoef;
-  int32_t* d_ffZ = nullptr;
+  int8_t* d_zslot = nullptr;  // form-factor slot of each Z in [0, 256), -1 if Z is not loaded
   uint64_t ff_version = 0;
   std::map<std::vector<double>, std::unique_ptr<GeoCache>> geos;
   std::map<int64_t, float2*> time_tw;
   std::map<int64_t, std::pair<void*, void*>> dft_ops;  // tensor-core DFT operands (hi, lo) per F and kind
-  int* d_status = nullptr;  // device status word: nonzero after a kernel's bounded wait ran out
+  int* d_status = nullptr;  // device status word: bits TACAW_STATUS_* (tacaw_internal.cuh)
   int64_t max_chunk_frames = 0;  // option: cap on frames per chunk (0 = automatic)
   int64_t max_slice_block = 0;   // option: cap on slices per block of a run (0 = automatic)
   int64_t min_wave_rows = 0;     // option: wave rows a slice launch should hold (0 = default)

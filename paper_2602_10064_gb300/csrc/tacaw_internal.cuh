@@ -43,6 +43,14 @@ struct SpreadKernel {
   float beta;  // exp(beta (sqrt(1 - z^2) - 1))
 };
 
+// Bits of the context's device status word, read and cleared by tacaw_check.
+constexpr int TACAW_STATUS_TIMEOUT = 1;  // a kernel's bounded wait ran out
+constexpr int TACAW_STATUS_SPECIES = 2;  // an atom's Z was not in the form-factor table
+
+// slot[j] = lut[Z[j]] (lut: 256 entries, -1 = not loaded); an unknown Z sets
+// TACAW_STATUS_SPECIES in *status and gets slot 0.
+cudaError_t launch_map_slots(const int32_t* Z, int64_t A, const int8_t* lut, int8_t* slot, int* status,
+                             cudaStream_t st);
 cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
                        int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
                        cudaStream_t st);

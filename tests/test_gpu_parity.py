@@ -128,6 +128,56 @@ def test_unknown_species_is_rejected(ctx, T):
     ctx.build_potential(T.params_of(w), dev(w.pos), dev(w.Z))
 
 
+def test_run_unknown_species_on_device_reported_by_check(ctx, T):
+    """tacaw_run maps device-resident Z on the device: an unknown species is reported by the next
+    tacaw_check (EINVAL), which clears it; with Z on the host the call itself rejects it."""
+    import torch
+    w = workloads.diamond_si(n_frames=2, grid=32, n_slices=2, reps=(1, 1, 1))
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    ctx.check()
+    Zbad = w.Z.copy()
+    Zbad[3] = 79
+    p, pr = T.params_of(w), T.probe_of(w)
+    out = torch.empty((1, w.n_frames, w.ny, w.nx), dtype=torch.float32, device="cuda")
+    T.tacaw_run(ctx.h, p, dev(w.pos), dev(Zbad), w.n_atoms, w.n_frames, pr, T.DFT_FP32, T.REDUCE_NONE, out)
+    with pytest.raises(T.TacawError) as ei:
+        ctx.check()
+    assert ei.value.code == T.TACAW_EINVAL
+    ctx.check()  # cleared
+    with pytest.raises(T.TacawError) as ei:
+        T.tacaw_run(ctx.h, p, dev(w.pos), Zbad, w.n_atoms, w.n_frames, pr, T.DFT_FP32, T.REDUCE_NONE, out)
+    assert ei.value.code == T.TACAW_EINVAL
+    good = ctx.run(p, dev(w.pos), dev(w.Z), pr).cpu().numpy()
+    ctx.check()
+    assert rel(good, oracle.tacaw(w)) < TOL_S
+
+
+def test_run_does_not_block_the_host(ctx, T):
+    """With every buffer on the device, tacaw_run only enqueues work: the call returns while
+    an earlier long run is still executing on the same stream."""
+    import time
+    import torch
+    w = workloads.diamond_si(n_frames=64, grid=256, n_slices=20, seed=46)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p, pr = T.params_of(w), T.probe_of(w)
+    pos, Z = dev(w.pos), dev(w.Z)
+    out = torch.empty((1, w.n_frames, w.ny, w.nx), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    T.tacaw_run(ctx.h, p, pos, Z, w.n_atoms, w.n_frames, pr, T.DFT_BF16X3, T.REDUCE_NONE, out, st)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    t0 = time.perf_counter()
+    for _ in range(4):
+        T.tacaw_run(ctx.h, p, pos, Z, w.n_atoms, w.n_frames, pr, T.DFT_BF16X3, T.REDUCE_NONE, out, st)
+    host_s = time.perf_counter() - t0
+    b.record(st)
+    torch.cuda.synchronize()
+    gpu_s = a.elapsed_time(b) / 1e3
+    ctx.check()
+    assert host_s < 0.5 * gpu_s, (host_s, gpu_s)
+
+
 @pytest.mark.parametrize("bl", [0.0, 0.8])
 def test_potential_rejects_band_beyond_two_thirds(ctx, T, bl):
     w = workloads.diamond_si(n_frames=1, grid=32, n_slices=2)
