@@ -20,8 +20,10 @@ namespace tacaw {
 // Per-kernel variants of the FFT pass kernels, chosen per transform length by the autotuner
 // (paper_2602_10064_gb300/tune.py), which times every variant on GB300 and writes
 // tuning_table.h.  Variant bits: 1 = radix-8 plans (512 and 1024 points), 2 = three resident
-// CTAs per SM (register cap 80) instead of two (128).  TACAW_TUNE_FORCE=v builds every kernel
-// as variant v (the tuner's measurement builds).
+// CTAs per SM (register cap 80) instead of two (128), 4 = column passes only: twice the
+// columns per CTA (one CTA of about 512 threads per SM, register cap 128), so that each load
+// instruction covers whole 128-byte lines.  TACAW_TUNE_FORCE=v builds every kernel as variant
+// v (the tuner's measurement builds).
 enum KernelId {
   K_SPLAT_ROW, K_COL_POT, K_ROW_POT_OUT, K_ROW_VT, K_COL_T, K_ROW_TOUT, K_PROBE_COL, K_PROBE_ROW,
   K_SLICE_ROW, K_SLICE_COL
@@ -35,8 +37,10 @@ namespace tacaw {
 template <int K, int N>
 struct Tuned {
   static constexpr int V = TACAW_TUNE_FORCE >= 0 ? TACAW_TUNE_FORCE : tuned_variant(K, N);
+  static constexpr bool COLUMN = K == K_COL_POT || K == K_COL_T || K == K_PROBE_COL || K == K_SLICE_COL;
   static constexpr int PLAN = V & 1;
-  static constexpr int MINB = (V & 2) ? 3 : 2;
+  static constexpr int WIDE = (COLUMN && (V & 4)) ? 1 : 0;
+  static constexpr int MINB = WIDE ? 1 : ((V & 2) ? 3 : 2);
 };
 
 // Elements per thread of the row and of the column transforms (8 or 16).
@@ -56,11 +60,13 @@ struct RowCfg {
   static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
 };
 
-template <int N>
+// Column passes: C columns per CTA (about 256 threads; WIDE doubles C, about 512 threads).
+template <int N, int WIDE = 0>
 struct ColCfg {
   static constexpr int E = FftPlan<N, TACAW_COL_E>::E;
   static constexpr int T = N / E;
-  static constexpr int C = (256 / T) > 32 ? 32 : ((256 / T) < 4 ? 4 : 256 / T);  // columns per CTA
+  static constexpr int C0 = (256 << WIDE) / T;
+  static constexpr int C = C0 > 32 ? 32 : (C0 < 4 ? 4 : C0);  // columns per CTA
   static constexpr int THREADS = C * T;
   static constexpr int SMEM = N * C * (int)sizeof(float2);
 };
@@ -345,10 +351,12 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::M
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
 template <int NY, bool ONE>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_COL_POT, NY>::MINB)
+__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREADS,
+                                  Tuned<K_COL_POT, NY>::MINB)
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
-  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  using CC = ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>;
+  constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_COL_POT, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -465,9 +473,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::MINB
 
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_COL_T, NY>::MINB)
+__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
+                                  Tuned<K_COL_T, NY>::MINB)
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
-  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  using CC = ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>;
+  constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_COL_T, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -517,10 +527,12 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::MI
 // Probe: psi0(k) = A(k) exp(-2 pi i k.r_p) amp, then a unitary inverse transform.
 // ============================================================================================
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_PROBE_COL, NY>::MINB)
+__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THREADS,
+                                  Tuned<K_PROBE_COL, NY>::MINB)
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey,
                 const float2* __restrict__ chi, int P, float amp, float2* __restrict__ Bpr) {
-  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  using CC = ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>;
+  constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_PROBE_COL, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -625,11 +637,13 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::M
 }
 
 template <int NY, bool LAST>
-__global__ void __launch_bounds__(ColCfg<NY>::THREADS, Tuned<K_SLICE_COL, NY>::MINB)
+__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THREADS,
+                                  Tuned<K_SLICE_COL, NY>::MINB)
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
-  constexpr int E = ColCfg<NY>::E, T = ColCfg<NY>::T, C = ColCfg<NY>::C;
+  using CC = ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>;
+  constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_SLICE_COL, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -743,11 +757,16 @@ cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, c
 template <int NY>
 static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                              float2* Ap, cudaStream_t st) {
-  const dim3 grid = batch_grid(b.Wp / ColCfg<NY>::C, nfs);
-  if (npair == 1)
-    k_col_pot<NY, true><<<grid, ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
-  else
-    k_col_pot<NY, false><<<grid, ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
+  using CC = ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>;
+  const dim3 grid = batch_grid(b.Wp / CC::C, nfs);
+  cudaError_t e;
+  if (npair == 1) {
+    if ((e = prep(k_col_pot<NY, true>, CC::SMEM)) != cudaSuccess) return e;
+    k_col_pot<NY, true><<<grid, CC::THREADS, CC::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
+  } else {
+    if ((e = prep(k_col_pot<NY, false>, CC::SMEM)) != cudaSuccess) return e;
+    k_col_pot<NY, false><<<grid, CC::THREADS, CC::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
@@ -782,7 +801,10 @@ cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, 
 template <int NY>
 static cudaError_t col_t_n(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
                            cudaStream_t st) {
-  k_col_t<NY><<<batch_grid(b.Wp / ColCfg<NY>::C, nfs), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(g, b, Bt, nfs,
+  using CC = ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>;
+  const cudaError_t e = prep(k_col_t<NY>, CC::SMEM);
+  if (e != cudaSuccess) return e;
+  k_col_t<NY><<<batch_grid(b.Wp / CC::C, nfs), CC::THREADS, CC::SMEM, st>>>(g, b, Bt, nfs,
                                                                                                    scale, At);
   return cudaGetLastError();
 }
@@ -804,7 +826,10 @@ cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int n
 template <int NY>
 static cudaError_t probe_col_n(const Geo& g, const Band& ap, const float2* ex, const float2* ey, const float2* chi,
                                int P, float amp, float2* Bpr, cudaStream_t st) {
-  k_probe_col<NY><<<batch_grid(ap.Wp / ColCfg<NY>::C, P), ColCfg<NY>::THREADS, ColCfg<NY>::SMEM, st>>>(
+  using CC = ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>;
+  const cudaError_t e = prep(k_probe_col<NY>, CC::SMEM);
+  if (e != cudaSuccess) return e;
+  k_probe_col<NY><<<batch_grid(ap.Wp / CC::C, P), CC::THREADS, CC::SMEM, st>>>(
       g, ap, ex, ey, chi, P, amp, Bpr);
   return cudaGetLastError();
 }
@@ -862,8 +887,11 @@ static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const floa
                                const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
                                float2* Apsi, float2* psi_k, cudaStream_t st) {
   const int nw = P * nfc;
-  const dim3 grid = batch_grid(b.Wp / ColCfg<NY>::C, nw);
-  constexpr int TH = ColCfg<NY>::THREADS, SM = ColCfg<NY>::SMEM;
+  using CC = ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>;
+  const dim3 grid = batch_grid(b.Wp / CC::C, nw);
+  constexpr int TH = CC::THREADS, SM = CC::SMEM;
+  cudaError_t e = last ? prep(k_slice_col<NY, true>, SM) : prep(k_slice_col<NY, false>, SM);
+  if (e != cudaSuccess) return e;
   if (last)
     k_slice_col<NY, true><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, Apsi, psi_k);
   else

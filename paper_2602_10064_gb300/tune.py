@@ -2,9 +2,10 @@
 
 Every FFT pass kernel (spreading row pass, potential and band-limit column passes, the row
 passes that form t, the multislice row and column passes) comes in variants: radix-16 or
-radix-8 plans (512 and 1024 points), and two or three resident CTAs per SM.  No single choice
-is best for all of them: on GB300 the radix-8 plans speed up the 1024-point row passes, and
-three CTAs per SM speed up the spreading pass but slow down the multislice row pass.
+radix-8 plans (512 and 1024 points), two or three resident CTAs per SM, and for the column
+passes twice the columns per CTA.  No single choice is best for all of them: on GB300 the
+radix-8 plans speed up the 1024-point row passes, and three CTAs per SM speed up the
+spreading pass but slow down the multislice row pass.
 
 This script builds the library once per variant (TACAW_TUNE_FORCE), times every kernel class
 at every transform length on representative runs with the library's own CUDA-event profiler,
@@ -13,7 +14,7 @@ replaces the default only when it is at least 2% faster.  Results of different v
 to FP32 rounding (the radix schedule changes the rounding order); the parity tests hold for
 every variant.
 
-    python -m paper_2602_10064_gb300.tune [--out PATH] [--variants 0 1 2 3]
+    python -m paper_2602_10064_gb300.tune [--out PATH] [--variants 0 1 ... 7]
 
 Needs a GPU.  Synthetic inputs come from the repository's `workloads` module.
 """
@@ -31,6 +32,8 @@ ROOT = os.path.dirname(PKG)
 # kernel class (library profiler name) -> KernelId in k_slices.cu
 KERNEL_IDS = {"splat_row": 0, "col_pot": 1, "row_pot_t": 2, "row_vt": 3, "col_t": 4, "row_tout": 5,
               "slice_row": 8, "slice_col": 9}
+# classes whose kernels take the column-width bit (variant & 4); the others ignore it
+COLUMN_CLASSES = {"col_pot", "col_t", "slice_col"}
 N_KERNELS = 10
 LENGTHS = (32, 64, 128, 256, 512, 1024)
 MIN_GAIN = 0.02
@@ -110,6 +113,8 @@ def choose(results: dict) -> list:
         base = results[0][key]
         v_best, t_best = 0, base
         for v, r in results.items():
+            if (v & 4) and cls not in COLUMN_CLASSES:
+                continue
             if key in r and r[key] < t_best:
                 v_best, t_best = v, r[key]
         if v_best != 0 and t_best > (1.0 - MIN_GAIN) * base:
@@ -126,7 +131,7 @@ def header(table: list, results: dict) -> str:
     lines = [
         "// Variant of each FFT pass kernel per transform length (see Tuned in k_slices.cu).",
         "// Written by paper_2602_10064_gb300/tune.py from CUDA-event timings of every variant on GB300",
-        "// (variant & 1: radix-8 plans; variant & 2: three CTAs per SM); milliseconds per variant:",
+        "// (variant & 1: radix-8 plans; & 2: three CTAs per SM; & 4: wide column CTAs); ms per variant:",
     ]
     for key in sorted(set().union(*(r.keys() for r in results.values()))):
         lines.append("//   " + key + ": " + ", ".join(f"v{v} {r[key]:.2f}" for v, r in sorted(results.items())
@@ -145,7 +150,7 @@ def header(table: list, results: dict) -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(PKG, "csrc", "tuning_table.h"))
-    ap.add_argument("--variants", type=int, nargs="*", default=[0, 1, 2, 3])
+    ap.add_argument("--variants", type=int, nargs="*", default=list(range(8)))
     ap.add_argument("--measure", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.measure is not None:

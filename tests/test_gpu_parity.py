@@ -354,6 +354,53 @@ def test_run_static_is_zero(ctx, T):
     assert np.abs(S).max() == 0.0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_run_rectangular_grid(ctx, T, prec):
+    w = rect_diamond(n_frames=12, seed=47)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    code = {"fp32": T.DFT_FP32, "bf16x3": T.DFT_BF16X3}[prec]
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w), precision=code).cpu().numpy()
+    assert S.shape == (1, 12, 32, 64)
+    assert rel(S, oracle.tacaw(w)) < TOL_S
+
+
+def test_run_without_atoms_is_zero(ctx, T):
+    """No atoms: every frame is the same vacuum wave, so the residual and S vanish exactly."""
+    import torch
+    w = workloads.diamond_si(n_frames=6, grid=32, n_slices=3, reps=(1, 1, 1))
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    pos = torch.zeros((6, 0, 3), dtype=torch.float32, device="cuda")
+    Z = torch.zeros((0,), dtype=torch.int32, device="cuda")
+    S = ctx.run(T.params_of(w), pos, Z, T.probe_of(w)).cpu().numpy()
+    ctx.check()
+    assert S.shape == (1, 6, 32, 32) and np.abs(S).max() == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_run_single_frame_is_zero(ctx, T, prec):
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=3, reps=(1, 1, 1))
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    code = {"fp32": T.DFT_FP32, "bf16x3": T.DFT_BF16X3}[prec]
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w), precision=code).cpu().numpy()
+    ctx.check()
+    assert np.abs(S).max() == 0.0
+
+
+def test_run_rejects_too_many_frames_or_probes(ctx, T):
+    import torch
+    w = workloads.diamond_si(n_frames=1, grid=32, n_slices=2, reps=(1, 1, 1))
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p, pr = T.params_of(w), T.probe_of(w)
+    out = torch.empty(1, dtype=torch.float32, device="cuda")
+    with pytest.raises(T.TacawError) as ei:
+        T.tacaw_run(ctx.h, p, dev(w.pos), dev(w.Z), w.n_atoms, 65536, pr, T.DFT_FP32, T.REDUCE_NONE, out)
+    assert ei.value.code == T.TACAW_EINVAL
+    scan = T.ProbeSpec(alpha_mrad=30.0, xy=np.zeros((65536, 2)))
+    with pytest.raises(T.TacawError) as ei:
+        T.tacaw_run(ctx.h, p, dev(w.pos), dev(w.Z), w.n_atoms, 1, scan, T.DFT_FP32, T.REDUCE_NONE, out)
+    assert ei.value.code == T.TACAW_EINVAL
+
+
 def test_run_host_buffers_match_device(ctx, T):
     import torch
     w = workloads.diamond_si(n_frames=8, grid=32, n_slices=4, seed=43)
