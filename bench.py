@@ -139,23 +139,28 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
-    """dram bytes per launch from the committed ncu summary, if it matches the current source."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def ncu_traffic(kernel, config, alg_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.md): the captured
+    ratio of DRAM to algorithmic bytes times this run's algorithmic bytes per launch, if the
+    row matches the config, the kernel class and the current CUDA sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    e = d.get(workload, {}).get(kernel)
-    if not e or e.get("src") != src_hash():
-        return None
-    return e.get("dram_bytes_per_launch")
+    for line in open(p):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 5 and cells[0] == config and cells[1] == kernel and cells[4] == src_hash():
+            try:
+                return float(cells[2]) * alg_bytes_per_launch
+            except ValueError:
+                return None
+    return None
 
 
 # FP32 lanes per SM (4 SMSPs x 32), SMs: the ALU roofline of the FFT kernels
 FP32_LANES, N_SM = 128, 152
 
 
-def roofline(prof, steps, wname, sm_mhz):
+def roofline(prof, steps, config, sm_mhz):
     name = max(prof, key=lambda k: prof[k][0])
     ms, nl, by, fl = prof[name]
     per_launch_s = ms / 1e3 / nl
@@ -177,7 +182,7 @@ def roofline(prof, steps, wname, sm_mhz):
         r["fp32_tflops_achieved"] = tfl
     r.update({"kernel": name, "launches_per_step": nl / steps, "ms_per_launch": per_launch_s * 1e3,
               "algorithmic_bytes_per_launch": by / nl, "algorithmic_flops_per_launch": fl / nl,
-              "traffic": ncu_traffic(name, wname), "peak_source": tag})
+              "traffic": ncu_traffic(name, config, by / nl), "peak_source": tag})
     return r
 
 
@@ -475,7 +480,7 @@ def main():
         "config": workload_config(w, args.workload, args.precision),
         "spectra_per_s": spectra, "px_slices_per_s": value * w.nx * w.ny,
         "step_ms": step_ms,
-        "roofline": roofline(prof, args.steps, w.name, clk.get("sm_mhz")),
+        "roofline": roofline(prof, args.steps, args.workload, clk.get("sm_mhz")),
         "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                         "gbs": v[2] / max(v[0], 1e-9) / 1e6, "tflops": v[3] / max(v[0], 1e-9) / 1e9}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
