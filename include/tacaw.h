@@ -23,7 +23,8 @@
  *    spatial frequency k = m / L (cycles per Angstrom, no 2 pi) with m = i for i < (n+1)/2
  *    and m = i - n otherwise.  Time-frequency bins are in the same order: bin m has
  *    f_m = m / (F dt).
- *  - Grids nx, ny must be powers of two in [32, 1024].
+ *  - Grids nx, ny must be powers of two in [32, 1024], or one of 96, 192, 384, 768 (3 * 2^k)
+ *    and 1152 (9 * 2^7: 0.1 A sampling of a ~110 A cell).
  *  - Units: Angstrom, eV, fs, mrad; potentials in V*A (projected), sigma in rad/(V*A).
  */
 #ifndef TACAW_H

@@ -55,7 +55,12 @@ double band_radius(const tacaw_params& p) {
   return p.bandlimit * (a < b ? a : b);
 }
 
-bool pow2_in_range(int n) { return n >= 32 && n <= 1024 && (n & (n - 1)) == 0; }
+// Transform lengths the slice kernels are built for: powers of two 32 .. 1024, 3 * 2^k for
+// 96 .. 768, and 1152 = 9 * 2^7.
+bool grid_supported(int n) {
+  if (n >= 32 && n <= 1024 && (n & (n - 1)) == 0) return true;
+  return n == 96 || n == 192 || n == 384 || n == 768 || n == 1152;
+}
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
@@ -208,8 +213,10 @@ bool has_aberrations(const tacaw_probe& pr) {
 
 int check_params(tacaw_ctx* ctx, const tacaw_params* p) {
   if (!p) return set_err(ctx, TACAW_EINVAL, "params is NULL");
-  if (!pow2_in_range(p->nx) || !pow2_in_range(p->ny))
-    return set_err(ctx, TACAW_EINVAL, "grid %dx%d: nx, ny must be powers of two in [32, 1024]", p->nx, p->ny);
+  if (!grid_supported(p->nx) || !grid_supported(p->ny))
+    return set_err(ctx, TACAW_EINVAL,
+                   "grid %dx%d: nx, ny must be powers of two in [32, 1024] or one of 96, 192, 384, 768, 1152",
+                   p->nx, p->ny);
   if (p->n_slices < 1 || p->n_slices > 256) return set_err(ctx, TACAW_EINVAL, "n_slices %d not in [1, 256]", p->n_slices);
   for (int i = 0; i < 3; ++i)
     if (!(p->cell[i] > 0.0) || !std::isfinite(p->cell[i])) return set_err(ctx, TACAW_EINVAL, "cell[%d] must be > 0", i);
@@ -381,12 +388,15 @@ int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
-  // FFT twiddle tables, FP64 on host: entries [N, 2N) hold exp(-2 pi i j / N)
-  std::vector<float2> tw(4096, make_float2(0.f, 0.f));
-  for (int N = 2; N <= 2048; N *= 2)
+  // FFT twiddle tables, FP64 on host: exp(-2 pi i j / N) at tw_offset(N) + j
+  std::vector<float2> tw(kTwiddleEntries, make_float2(0.f, 0.f));
+  std::vector<int> lengths;
+  for (int N = 2; N <= 2048; N *= 2) lengths.push_back(N);
+  for (int N : kTwiddleOtherLengths) lengths.push_back(N);
+  for (int N : lengths)
     for (int j = 0; j < N; ++j) {
       const double a = -2.0 * M_PI * (double)j / (double)N;
-      tw[N + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+      tw[tw_offset(N) + j] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
   if (owned_alloc(ctx, &ctx->tw, tw.size()) != TACAW_OK ||
       cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||

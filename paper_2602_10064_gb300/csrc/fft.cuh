@@ -1,4 +1,5 @@
-// Device FFT engine for the slice kernels.
+// Device FFT engine for the slice kernels (lengths: powers of two 32 .. 2048, 3 * 2^k for 96 ..
+// 768, and 1152).
 //
 // Every 2D transform of the hot path (potential, transmission band limit, the slice step of
 // the multislice chain in Methods "Multislice Propagation") is split into 1D transforms along
@@ -132,19 +133,83 @@ __device__ __forceinline__ void dft16(float2* u) {
   }
 }
 
+// X[k] = sum_n u[n] exp(SIGN 2 pi i n k / 3).
+template <int SIGN>
+__device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
+  const float h = 0.86602540378443865f;  // sin(pi / 3)
+  const float2 s = a1 + a2, d = mul_si<SIGN>(a1 - a2);
+  const float2 m = a0 - 0.5f * s;
+  a0 = a0 + s;
+  a1 = m + h * d;
+  a2 = m - h * d;
+}
+
+// exp(SIGN 2 pi i j / 12) for the small j a radix-12 butterfly needs.
+template <int SIGN>
+__device__ __forceinline__ float2 w12(int j) {
+  const float h = 0.86602540378443865f;
+  float c, s;
+  switch (j % 12) {
+    case 0: c = 1.f; s = 0.f; break;
+    case 1: c = h; s = 0.5f; break;
+    case 2: c = 0.5f; s = h; break;
+    case 3: c = 0.f; s = 1.f; break;
+    case 4: c = -0.5f; s = h; break;
+    case 5: c = -h; s = 0.5f; break;
+    case 6: c = -1.f; s = 0.f; break;
+    case 7: c = -h; s = -0.5f; break;
+    case 8: c = -0.5f; s = -h; break;
+    case 9: c = 0.f; s = -1.f; break;
+    case 10: c = 0.5f; s = -h; break;
+    default: c = h; s = -0.5f; break;
+  }
+  return make_float2(c, SIGN < 0 ? -s : s);
+}
+
+// Radix-12 as 4 x 3: radix-4 over n1 (stride 3), twiddle w12^(n2 k1), radix-3 over n2.
+template <int SIGN>
+__device__ __forceinline__ void dft12(float2* u) {
+  float2 y[3][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    y[n2][0] = u[n2];
+    y[n2][1] = u[3 + n2];
+    y[n2][2] = u[6 + n2];
+    y[n2][3] = u[9 + n2];
+    dft4<SIGN>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w12<SIGN>(n2 * k1));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1];
+    dft3<SIGN>(a0, a1, a2);
+    u[k1] = a0;
+    u[k1 + 4] = a1;
+    u[k1 + 8] = a2;
+  }
+}
+
 template <int R, int SIGN>
 __device__ __forceinline__ void dft_r(float2* u) {
   if constexpr (R == 2) dft2<SIGN>(u);
+  else if constexpr (R == 3) dft3<SIGN>(u[0], u[1], u[2]);
   else if constexpr (R == 4) dft4<SIGN>(u);
   else if constexpr (R == 8) dft8<SIGN>(u);
+  else if constexpr (R == 12) dft12<SIGN>(u);
   else dft16<SIGN>(u);
 }
 
-// Elements per thread (E) for a transform of length N: 8 or 16 (8 for N <= 64).  A kernel
-// picks E per pass direction; T = N / E threads share one transform.
+// Lengths 3 * 2^k (96 .. 768) and 9 * 2^7 (1152) besides the powers of two.
+__host__ __device__ constexpr bool fft_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Elements per thread (E) for a transform of length N: 8 or 16 for powers of two (8 for
+// N <= 64), 12 for the lengths with a factor 3.  A kernel picks E per pass direction (powers
+// of two); T = N / E threads share one transform.
 template <int N, int EPREF>
 struct FftPlan {
-  static constexpr int E = (N <= 64) ? 8 : EPREF;
+  static constexpr int E = !fft_pow2(N) ? 12 : ((N <= 64) ? 8 : EPREF);
   static constexpr int T = N / E;
 };
 
@@ -200,7 +265,7 @@ __device__ __forceinline__ void fft_pass(float2 (&v)[E], float2* sm, const Idx& 
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int bi = t + T * b;
-    const int k = bi & (NS - 1);
+    const int k = fft_pow2(NS) ? (bi & (NS - 1)) : (int)((unsigned)bi % (unsigned)NS);
     float2 u[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) u[i] = v[b + B * i];
@@ -287,6 +352,29 @@ __device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const Idx& idx, 
     fft_pass<2048, E, 16, 1, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<2048, E, 16, 16, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<2048, E, 8, 256, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 12 && N == 96) {
+    fft_pass<96, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<96, E, 4, 12, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<96, E, 2, 48, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 12 && N == 192) {
+    fft_pass<192, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<192, E, 4, 12, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<192, E, 4, 48, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 12 && N == 384) {
+    fft_pass<384, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<384, E, 4, 12, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<384, E, 4, 48, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<384, E, 2, 192, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 12 && N == 768) {
+    fft_pass<768, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<768, E, 4, 12, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<768, E, 4, 48, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<768, E, 4, 192, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 12 && N == 1152) {
+    fft_pass<1152, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1152, E, 12, 12, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1152, E, 4, 144, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1152, E, 2, 576, SIGN, true>(v, sm, idx, t, tw, sync);
   } else {
     static_assert(N == 32, "unsupported FFT length");
   }

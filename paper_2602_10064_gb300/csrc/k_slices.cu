@@ -40,7 +40,10 @@ struct Tuned {
   static constexpr bool COLUMN = K == K_COL_POT || K == K_COL_T || K == K_PROBE_COL || K == K_SLICE_COL;
   static constexpr int PLAN = V & 1;
   static constexpr int WIDE = (COLUMN && (V & 4)) ? 1 : 0;
-  static constexpr int MINB = WIDE ? 1 : ((V & 2) ? 3 : 2);
+  // resident CTAs per SM requested for a CTA of `threads`: 512 (variant & 2: 768) threads per SM
+  static constexpr int minb(int threads) {
+    return ((V & 2) ? 768 : 512) / threads > 1 ? ((V & 2) ? 768 : 512) / threads : 1;
+  }
 };
 
 // Elements per thread of the row and of the column transforms (8 or 16).
@@ -55,9 +58,10 @@ template <int N>
 struct RowCfg {
   static constexpr int E = FftPlan<N, TACAW_ROW_E>::E;
   static constexpr int T = N / E;
-  static constexpr int THREADS = (32 * T) < 256 ? 32 * T : 256;
-  static constexpr int G = THREADS / T;  // rows per CTA, one transform group each
+  static constexpr int G = (256 / T) > 32 ? 32 : ((256 / T) < 1 ? 1 : 256 / T);  // rows per CTA
+  static constexpr int THREADS = G * T;  // one transform group of T threads per row
   static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
+  static_assert(T <= 32 || T % 32 == 0, "a row group larger than a warp must be whole warps");
 };
 
 // Column passes: C columns per CTA (about 256 threads; WIDE doubles C, about 512 threads).
@@ -230,6 +234,18 @@ cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx
 // a2: potential.  Row pass: spread the atoms of one slice and one species pair onto G rows
 // (gather per grid point, candidates in atom order, so the sum is deterministic), then FFT_x.
 // ============================================================================================
+// x mod n for 0 <= x < 3 n (any n, no division).
+__device__ __forceinline__ int wrap3(int x, int n) {
+  x -= (x >= n) ? n : 0;
+  return x - ((x >= n) ? n : 0);
+}
+// The same for a compile-time n (a mask when n is a power of two).
+template <int N>
+__device__ __forceinline__ int wrap3(int x) {
+  if constexpr (fft_pow2(N)) return x & (N - 1);
+  else return wrap3(x, N);
+}
+
 __device__ __forceinline__ float es_kernel(float z, float beta) {
   const float a = 1.f - z * z;
   return a > 0.f ? expf(beta * (sqrtf(a) - 1.f)) : 0.f;
@@ -248,7 +264,7 @@ struct SplatSmem {
 };
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::minb(RowCfg<NX>::THREADS))
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
                 int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::M
       const int slot = r.jslot >> 24;
       if ((slot >> 1) == pair) {
         const int iy0 = r.ixy >> 16;
-        const int rr = (iy0 + 1 - h - y0 + 2 * ny) & (ny - 1);
+        const int rr = wrap3(iy0 + 1 - h - y0 + 2 * ny, ny);
         cand = (rr < G) || (rr + W2 - 1 >= ny);
       }
     }
@@ -305,7 +321,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::M
       const int ci = before + __popc(bal & ((1u << lane) - 1u));
       cfx[ci] = r.fx;
       cfy[ci] = r.fy;
-      cx0[ci] = ((r.ixy & 0xffff) + 1 - h + geo.nx) & (geo.nx - 1);
+      cx0[ci] = wrap3<NX>((r.ixy & 0xffff) + 1 - h + NX);
       ciy[ci] = (r.ixy >> 16) | (((r.jslot >> 24) & 1) << 16);
     }
     __syncthreads();
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::M
         phx[c * SPREAD_MAX_W + k] = es_kernel(((float)(k + 1 - h) - cfx[c]) / (float)h, sk.beta);
       } else {
         const int gg = k - W2;
-        int d = (y0 + gg - (ciy[c] & 0xffff) + ny) & (ny - 1);
+        int d = wrap3(y0 + gg - (ciy[c] & 0xffff) + ny, ny);
         if (d > ny / 2) d -= ny;
         phy[c * G + gg] = (d >= 1 - h && d <= h) ? es_kernel(((float)d - cfy[c]) / (float)h, sk.beta) : 0.f;
       }
@@ -331,9 +347,9 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::M
       if (wy == 0.f) continue;
       const int x0 = cx0[c];
       const bool im = (ciy[c] >> 16) != 0;
-      const int d = (x0 - t) & (NX - 1);
+      const int d = wrap3<NX>(x0 - t + NX);
       for (int off = (T - d % T) % T; off < W2; off += T) {
-        const int x = (x0 + off) & (NX - 1);
+        const int x = wrap3<NX>(x0 + off);
         const float a = wy * phx[c * SPREAD_MAX_W + off];
         if (im) arow[x].y += a;
         else arow[x].x += a;
@@ -345,14 +361,15 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::M
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = acc[g * NX + t + T * e];
   __syncthreads();  // the FFT scratch of one group overlaps the accumulators of the next
-  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+                  group_sync<T>(g));
   store_row_compact<NX>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
 }
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
 template <int NY, bool ONE>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREADS,
-                                  Tuned<K_COL_POT, NY>::MINB)
+                                  Tuned<K_COL_POT, NY>::minb(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREADS))
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
   using CC = ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>;
@@ -365,7 +382,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREAD
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C> idx{c};
   const BlockSync sync;
-  const float2* tw = geo.tw + NY;
+  const float2* tw = geo.tw + tw_offset(NY);
   if (ONE) {
     // one species pair: no accumulator held across the transforms
     const float2* src = Bp + (size_t)fs * NY * b.Wp + cc;
@@ -404,7 +421,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREAD
 // Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
 // t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>::MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>::minb(RowCfg<NX>::THREADS))
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
@@ -418,7 +435,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>:
   const auto sync = group_sync<T>(g);
   float2 v[E];
   load_row_compact<NX>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1, PL>(v, sm, idx, t, geo.tw + NX, sync);
+  fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
   const size_t row = ((size_t)fs * ny + y) * NX;
   if (mode == 0) {
 #pragma unroll
@@ -436,7 +453,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>:
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1, PL>(v, sm, idx, t, geo.tw + NX, sync);
+  fft<NX, -1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>:
 // a3: transmission from a stored V.
 // ============================================================================================
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::minb(RowCfg<NX>::THREADS))
     k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
              float2* __restrict__ out) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
@@ -467,14 +484,15 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::MINB
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+                  group_sync<T>(g));
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
-                                  Tuned<K_COL_T, NY>::MINB)
+                                  Tuned<K_COL_T, NY>::minb(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS))
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
   using CC = ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
@@ -486,7 +504,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C> idx{c};
   const BlockSync sync;
-  const float2* tw = geo.tw + NY;
+  const float2* tw = geo.tw + tw_offset(NY);
   const float2* src = Bt + (size_t)fs * NY * b.Wp + cc;
   float2 v[E];
 #pragma unroll
@@ -506,7 +524,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
 
 // Row pass out of the band limit: IFFT_x -> t (full row).
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::minb(RowCfg<NX>::THREADS))
     k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   constexpr int PL = Tuned<K_ROW_TOUT, NX>::PLAN;
@@ -517,7 +535,8 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::MI
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, At + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+                  group_sync<T>(g));
   float2* dst = tout + ((size_t)fs * ny + y) * NX;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[t + T * e] = v[e];
@@ -528,7 +547,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::MI
 // ============================================================================================
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THREADS,
-                                  Tuned<K_PROBE_COL, NY>::MINB)
+                                  Tuned<K_PROBE_COL, NY>::minb(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THREADS))
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey,
                 const float2* __restrict__ chi, int P, float amp, float2* __restrict__ Bpr) {
   using CC = ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>;
@@ -548,14 +567,14 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THRE
     v[e] = (abs(n) <= nb) ? amp * cmul(exv, ey[(size_t)p * NY + row]) : make_float2(0.f, 0.f);
     if (chi && abs(n) <= nb) v[e] = cmul(v[e], chi[(size_t)row * ap.Wp + cc]);
   }
-  fft<NY, +1, PL>(v, sm, ColIdx<C>{c}, t, geo.tw + NY, BlockSync{});
+  fft<NY, +1, PL>(v, sm, ColIdx<C>{c}, t, geo.tw + tw_offset(NY), BlockSync{});
   float2* dst = Bpr + (size_t)p * NY * ap.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * ap.Wp] = v[e];
 }
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_PROBE_ROW, NX>::MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_PROBE_ROW, NX>::minb(RowCfg<NX>::THREADS))
     k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   constexpr int PL = Tuned<K_PROBE_ROW, NX>::PLAN;
@@ -566,7 +585,8 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_PROBE_ROW, NX>::M
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, Bpr + ((size_t)p * ny + y) * ap.Wp, ap, t);
-  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + NX, group_sync<T>(g));
+  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+                  group_sync<T>(g));
   float2* dst = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[t + T * e] = scale * v[e];
@@ -584,7 +604,7 @@ struct SliceRowSmem {
 };
 
 template <int NX, bool FIRST, bool PLANE, bool TF>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::MINB)
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::minb(RowCfg<NX>::THREADS))
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
                 float2* __restrict__ Bpsi) {
@@ -612,7 +632,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::M
   float2* tst = reinterpret_cast<float2*>(smraw + RowCfg<NX>::SMEM) + g * NX;
   if (TF) {
     load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
-    fft<NX, +1, PL>(v, sm, idx, t, geo.tw + NX, sync);
+    fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
 #pragma unroll
     for (int e = 0; e < E; ++e) tst[t + T * e] = v[e];
   }
@@ -628,17 +648,17 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::M
     }
   } else {
     load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
-    fft<NX, +1, PL>(v, sm, idx, t, geo.tw + NX, sync);
+    fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmul(v[e], TF ? tst[t + T * e] : trow[t + T * e]);
   }
-  fft<NX, -1, PL>(v, sm, idx, t, geo.tw + NX, sync);
+  fft<NX, -1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
   store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
 }
 
 template <int NY, bool LAST>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THREADS,
-                                  Tuned<K_SLICE_COL, NY>::MINB)
+                                  Tuned<K_SLICE_COL, NY>::minb(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THREADS))
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
@@ -652,7 +672,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THRE
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C> idx{c};
   const BlockSync sync;
-  const float2* tw = geo.tw + NY;
+  const float2* tw = geo.tw + tw_offset(NY);
   const float2* src = Bpsi + (size_t)w * NY * b.Wp + cc;
   float2 v[E];
 #pragma unroll
@@ -724,15 +744,20 @@ static cudaError_t prep(K kernel, int smem) {
   return cudaSuccess;
 }
 
-#define TACAW_DISPATCH(N, FN, ...)     \
-  switch (N) {                         \
-    case 32: return FN<32>(__VA_ARGS__);   \
-    case 64: return FN<64>(__VA_ARGS__);   \
-    case 128: return FN<128>(__VA_ARGS__); \
-    case 256: return FN<256>(__VA_ARGS__); \
-    case 512: return FN<512>(__VA_ARGS__); \
+#define TACAW_DISPATCH(N, FN, ...)       \
+  switch (N) {                           \
+    case 32: return FN<32>(__VA_ARGS__);     \
+    case 64: return FN<64>(__VA_ARGS__);     \
+    case 96: return FN<96>(__VA_ARGS__);     \
+    case 128: return FN<128>(__VA_ARGS__);   \
+    case 192: return FN<192>(__VA_ARGS__);   \
+    case 256: return FN<256>(__VA_ARGS__);   \
+    case 384: return FN<384>(__VA_ARGS__);   \
+    case 512: return FN<512>(__VA_ARGS__);   \
+    case 768: return FN<768>(__VA_ARGS__);   \
     case 1024: return FN<1024>(__VA_ARGS__); \
-    default: return cudaErrorInvalidValue; \
+    case 1152: return FN<1152>(__VA_ARGS__); \
+    default: return cudaErrorInvalidValue;   \
   }
 
 template <int NX>

@@ -51,7 +51,7 @@ struct tacaw_ctx {
   uint64_t budget = 0;
   std::string err;
   std::recursive_mutex mu;
-  float2* tw = nullptr;  // FFT twiddles: length-N table at tw + N (N = 2 .. 2048)
+  float2* tw = nullptr;  // FFT twiddles: length-N table at tw + tw_offset(N)
   std::vector<int32_t> ffZ;
   std::vector<double> ffcoef;
   int8_t* d_zslot = nullptr;  // form-factor slot of each Z in [0, 256), -1 if Z is not loaded

@@ -20,8 +20,23 @@ struct Band {
 // Grid shape plus the FFT twiddle tables (table for length N starts at tw + N).
 struct Geo {
   int nx, ny;
-  const float2* tw;
+  const float2* tw;  // the context's twiddle tables: length n at tw + tw_offset(n)
 };
+
+// Layout of the context's twiddle table: exp(-2 pi i j / n), j < n, at [tw_offset(n),
+// tw_offset(n) + n): the powers of two 2 .. 2048 at offset n (packed into [2, 4096)), then the
+// lengths with a factor 3 one after the other.
+__host__ __device__ constexpr int tw_offset(int n) {
+  return (n & (n - 1)) == 0 ? n
+         : n == 96          ? 4096
+         : n == 192         ? 4096 + 96
+         : n == 384         ? 4096 + 288
+         : n == 768         ? 4096 + 672
+         : n == 1152        ? 4096 + 1440
+                            : -1;
+}
+constexpr int kTwiddleEntries = 4096 + 2592;
+constexpr int kTwiddleOtherLengths[5] = {96, 192, 384, 768, 1152};
 
 // One atom after binning, in the order of its slice list.  ix0/iy0 = floor of the grid
 // coordinate (x wrapped into [0, Lx), times nx / Lx, in FP64), fx/fy the remainder.

@@ -142,7 +142,7 @@ def header(table: list, results: dict) -> str:
               "constexpr int tuned_variant(int kernel, int n) {",
               "  int l = 0;",
               "  while ((32 << l) < n) ++l;",
-              "  return (kernel >= 0 && kernel < 10 && l < 6) ? kTunedVariant[kernel][l] : 0;",
+              "  return (kernel >= 0 && kernel < 10 && l < 6 && (32 << l) == n) ? kTunedVariant[kernel][l] : 0;",
               "}", "", "}  // namespace tacaw", ""]
     return "\n".join(lines)
 

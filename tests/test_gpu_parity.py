@@ -90,11 +90,21 @@ def three_species():
     return w
 
 
-@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_half", "three_species"])
+def grid_diamond(nx, ny, n_frames=2, n_slices=3, reps=(1, 1, 1), seed=33):
+    """Diamond Si on an nx x ny grid (any supported lengths, not only powers of two)."""
+    w = workloads.diamond_si(n_frames=n_frames, grid=nx, n_slices=n_slices, reps=reps, seed=seed)
+    w.ny = ny
+    return w
+
+
+@pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_half", "three_species", "g96", "g192x96",
+                                  "g1152x96"])
 def test_potential_parity(ctx, T, case):
     w = {"c1": lambda: workloads.diamond_si(n_frames=2), "rocksalt": small_rocksalt, "rect": rect_diamond,
          "bl_half": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4),
-         "three_species": three_species}[case]()
+         "three_species": three_species, "g96": lambda: grid_diamond(96, 96),
+         "g192x96": lambda: grid_diamond(192, 96, reps=(2, 1, 1)),
+         "g1152x96": lambda: grid_diamond(1152, 96, n_slices=2)}[case]()
     kw = {"bandlimit": 0.5} if case == "bl_half" else {}
     ctx.load_form_factors(w.form_Z, w.form_coef)
     p = T.params_of(w, **kw)
@@ -209,11 +219,12 @@ def test_propagate_without_band_limit(ctx, T):
     assert abs(np.sum(np.abs(psi) ** 2) - 1) < 1e-5
 
 
-def test_bad_grid_is_rejected(ctx, T):
+@pytest.mark.parametrize("n", [100, 48, 1536, 2048, 16])
+def test_bad_grid_is_rejected(ctx, T, n):
     w = workloads.diamond_si(n_frames=1, grid=32, n_slices=2)
     ctx.load_form_factors(w.form_Z, w.form_coef)
     with pytest.raises(T.TacawError):
-        ctx.build_potential(T.params_of(w, nx=100), dev(w.pos), dev(w.Z))
+        ctx.build_potential(T.params_of(w, nx=n), dev(w.pos), dev(w.Z))
 
 
 # ------------------------------------------------------------------------------------------
@@ -234,7 +245,8 @@ def test_transmission_parity(ctx, T, blt):
 # ------------------------------------------------------------------------------------------
 # a4/a5 multislice
 # ------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("case", ["plane", "probe", "rocksalt", "rect", "one_slice"])
+@pytest.mark.parametrize("case", ["plane", "probe", "rocksalt", "rect", "one_slice", "g192", "g96x384",
+                                  "g96x1152"])
 def test_propagate_parity(ctx, T, case):
     if case == "plane":
         w = workloads.diamond_si(n_frames=2)
@@ -245,6 +257,13 @@ def test_propagate_parity(ctx, T, case):
         w = small_rocksalt(n_frames=2)
     elif case == "rect":
         w = rect_diamond(n_frames=2)
+    elif case == "g192":
+        w = grid_diamond(192, 192, n_slices=4)
+    elif case == "g96x384":
+        w = grid_diamond(96, 384, n_slices=3, reps=(1, 2, 1))
+        w.alpha_mrad, w.probes = 25.0, np.array([[0.0, 0.0], [3.3, 7.1]])
+    elif case == "g96x1152":
+        w = grid_diamond(96, 1152, n_frames=1, n_slices=2, reps=(1, 2, 1))
     else:
         w = workloads.diamond_si(n_frames=2, grid=32, n_slices=1)
     ctx.load_form_factors(w.form_Z, w.form_coef)
@@ -259,19 +278,24 @@ def test_propagate_parity(ctx, T, case):
             assert rel(psi[ip, f], ref[ip]) < TOL_FIELD, (f, ip, rel(psi[ip, f], ref[ip]))
 
 
-def test_vacuum_is_exact_fresnel(ctx, T):
-    N, L, Lz, S = 64, 12.0, 21.0, 5
-    p = T.make_params(N, N, S, (L, L, Lz))
+@pytest.mark.parametrize("NX,NY", [(64, 64), (96, 96), (192, 192), (384, 384), (768, 768), (1152, 96),
+                                   (96, 384)])
+def test_vacuum_is_exact_fresnel(ctx, T, NX, NY):
+    """No potential: the exit wave is the probe times the mask and the Fresnel factor of the
+    whole thickness, exactly; every transform length and both axes of the engine."""
+    L, Lz, S = 12.0, 21.0, 5
+    Lx, Ly = L * NX / 64, L * NY / 64
+    p = T.make_params(NX, NY, S, (Lx, Ly, Lz))
     fz, fc = workloads.placeholder_form_factors([14])
     ctx.load_form_factors(fz, fc)
     import torch
-    V = torch.zeros((1, S, N, N), dtype=torch.float32, device="cuda")
+    V = torch.zeros((1, S, NY, NX), dtype=torch.float32, device="cuda")
     pr = T.ProbeSpec(40.0, np.array([[1.3, 2.9]]))
     psi = ctx.propagate(p, V, pr).cpu().numpy()[0, 0]
-    op = oracle.params(N, N, S, (L, L, Lz))
-    psi0 = oracle.fft2(oracle.probe(op, 40.0, 1.3, 2.9), -1) / N
-    k = np.fft.fftfreq(N, d=L / N)
-    k2 = k[:, None] ** 2 + k[None, :] ** 2
+    op = oracle.params(NX, NY, S, (Lx, Ly, Lz))
+    psi0 = np.fft.fft2(oracle.probe(op, 40.0, 1.3, 2.9)) / np.sqrt(NX * NY)
+    kx, ky = np.fft.fftfreq(NX, d=Lx / NX), np.fft.fftfreq(NY, d=Ly / NY)
+    k2 = kx[None, :] ** 2 + ky[:, None] ** 2
     want = psi0 * oracle.mask(op) * np.exp(-1j * np.pi * oracle.wavelength(100e3) * Lz * k2)
     assert rel(psi, want) < TOL_FIELD
 
@@ -352,6 +376,16 @@ def test_run_static_is_zero(ctx, T):
     ctx.load_form_factors(w.form_Z, w.form_coef)
     S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
     assert np.abs(S).max() == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_run_grid_with_factor_three(ctx, T, prec):
+    w = grid_diamond(96, 192, n_frames=10, n_slices=4, reps=(1, 2, 1), seed=48)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    code = {"fp32": T.DFT_FP32, "bf16x3": T.DFT_BF16X3}[prec]
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w), precision=code).cpu().numpy()
+    assert S.shape == (1, 10, 192, 96)
+    assert rel(S, oracle.tacaw(w)) < TOL_S
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])

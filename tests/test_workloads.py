@@ -67,4 +67,4 @@ def test_minimal_example_shape():
     w = workloads.minimal_example_si(n_frames=2)
     assert w.n_atoms == 16000 and w.n_slices == 54
     assert abs(w.cell[0] - 108.62) < 1e-9 and abs(w.cell[2] - 27.155) < 1e-9
-    assert abs(w.cell[0] / w.nx - 0.1) < 0.01  # ~0.1 A sampling
+    assert w.nx == w.ny == 1152 and w.cell[0] / w.nx <= 0.1  # 0.1 A sampling, padded

@@ -262,11 +262,12 @@ def config4(n_frames=2048, grid=1024, seed=4):
                       name=f"c4-diamond-si-{n_frames}x{grid}sq")
 
 
-def minimal_example_si(n_frames=200, grid=1024, n_slices=54, seed=6, n_scan=0):
+def minimal_example_si(n_frames=200, grid=1152, n_slices=54, seed=6, n_scan=0):
     """The shape of the paper's minimal example (Supplement, "Minimal Working Example"):
     diamond Si a = 5.431 A, 20 x 20 x 5 cells (16,000 atoms, 108.62 x 108.62 x 27.155 A), 200
-    frames 10 fs apart, 100 keV, ~0.1 A sampling (1024^2: 0.106 A), slices of ~0.5 A (54).
-    Thermal-like seeded displacements (32 modes, 0.06 A RMS) stand in for the MLIP MD."""
+    frames 10 fs apart, 100 keV, 0.1 A sampling (1086 points, padded to 1152^2: 0.094 A),
+    slices of ~0.5 A (54).  Thermal-like seeded displacements (32 modes, 0.06 A RMS) stand in
+    for the MLIP MD."""
     reps = (20, 20, 5)
     R, Z, cell = diamond(5.431, reps)
     rng = SplitMix64(seed)
