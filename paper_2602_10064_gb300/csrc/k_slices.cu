@@ -740,7 +740,8 @@ __global__ void k_build_mtab(int nx, int ny, Band b, int npair, int nslot, const
 // ============================================================================================
 template <class K>
 static cudaError_t prep(K kernel, int smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // opt in above 46 KB: some kernels add a little static shared memory to the dynamic amount
+  if (smem > 46 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return cudaSuccess;
 }
 

@@ -35,7 +35,7 @@ KERNEL_IDS = {"splat_row": 0, "col_pot": 1, "row_pot_t": 2, "row_vt": 3, "col_t"
 # classes whose kernels take the column-width bit (variant & 4); the others ignore it
 COLUMN_CLASSES = {"col_pot", "col_t", "slice_col"}
 N_KERNELS = 10
-LENGTHS = (32, 64, 128, 256, 512, 1024)
+LENGTHS = (32, 64, 128, 256, 512, 1024, 96, 192, 384, 768, 1152)
 MIN_GAIN = 0.02
 
 
@@ -51,6 +51,9 @@ def cases():
         ("scan-256", 256, lambda: workloads.config3(n_frames=16, seed=13)),
         ("rocksalt-512", 512, lambda: workloads.config2(n_frames=128, seed=14)),
         ("diamond-1024", 1024, lambda: workloads.config4(n_frames=64, seed=15)),
+        ("diamond-768", 768, lambda: workloads.diamond_si(n_frames=64, grid=768, n_slices=20, seed=16,
+                                                           reps=(8, 8, 2))),
+        ("minimal-example-1152", 1152, lambda: workloads.minimal_example_si(n_frames=16, seed=17)),
     ]
 
 
@@ -137,12 +140,15 @@ def header(table: list, results: dict) -> str:
         lines.append("//   " + key + ": " + ", ".join(f"v{v} {r[key]:.2f}" for v, r in sorted(results.items())
                                                   if key in r))
     lines += ["#pragma once", "", "namespace tacaw {", "",
-              "// [kernel][log2(N) - 5] for N = 32 .. 1024",
-              "constexpr int kTunedVariant[10][6] = {"] + rows + ["};", "",
+              "// transform lengths of the columns of kTunedVariant",
+              "constexpr int kTunedLengths[11] = {" + ", ".join(str(n) for n in LENGTHS) + "};",
+              "",
+              "// [kernel][index of N in kTunedLengths]",
+              "constexpr int kTunedVariant[10][11] = {"] + rows + ["};", "",
               "constexpr int tuned_variant(int kernel, int n) {",
-              "  int l = 0;",
-              "  while ((32 << l) < n) ++l;",
-              "  return (kernel >= 0 && kernel < 10 && l < 6 && (32 << l) == n) ? kTunedVariant[kernel][l] : 0;",
+              "  for (int l = 0; l < 11; ++l)",
+              "    if (kTunedLengths[l] == n) return (kernel >= 0 && kernel < 10) ? kTunedVariant[kernel][l] : 0;",
+              "  return 0;",
               "}", "", "}  // namespace tacaw", ""]
     return "\n".join(lines)
 

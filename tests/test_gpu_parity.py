@@ -98,13 +98,15 @@ def grid_diamond(nx, ny, n_frames=2, n_slices=3, reps=(1, 1, 1), seed=33):
 
 
 @pytest.mark.parametrize("case", ["c1", "rocksalt", "rect", "bl_half", "three_species", "g96", "g192x96",
-                                  "g1152x96"])
+                                  "g1152x96", "g768x96", "g384x192"])
 def test_potential_parity(ctx, T, case):
     w = {"c1": lambda: workloads.diamond_si(n_frames=2), "rocksalt": small_rocksalt, "rect": rect_diamond,
          "bl_half": lambda: workloads.diamond_si(n_frames=2, grid=64, n_slices=4),
          "three_species": three_species, "g96": lambda: grid_diamond(96, 96),
          "g192x96": lambda: grid_diamond(192, 96, reps=(2, 1, 1)),
-         "g1152x96": lambda: grid_diamond(1152, 96, n_slices=2)}[case]()
+         "g1152x96": lambda: grid_diamond(1152, 96, n_slices=2),
+         "g768x96": lambda: grid_diamond(768, 96, n_slices=2),
+         "g384x192": lambda: grid_diamond(384, 192, n_slices=2, reps=(2, 1, 1))}[case]()
     kw = {"bandlimit": 0.5} if case == "bl_half" else {}
     ctx.load_form_factors(w.form_Z, w.form_coef)
     p = T.params_of(w, **kw)
