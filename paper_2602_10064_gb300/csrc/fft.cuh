@@ -12,8 +12,10 @@
 // exit, so global loads and stores of a row are coalesced (consecutive t, consecutive
 // addresses).  A pass of radix R (R divides E) runs E/R butterflies per thread; the last pass
 // lands in the owner's own registers, so an N = R1*R2*R3 transform makes two shared-memory
-// exchanges.  Each group synchronises only itself (__syncwarp, or a named barrier when a
-// transform spans several warps), so the warps of a CTA never wait on one another.
+// exchanges (three for the four-pass plans of 384, 768 and 1152 points).  Each row group
+// synchronises only itself (__syncwarp, or a named barrier when a transform spans whole
+// warps), so the warps of a CTA never wait on one another; column transforms interleave
+// several columns and use the CTA barrier.
 //
 // Twiddles come from a table tw_N[j] = exp(-2 pi i j / N) built on the host in FP64 and
 // rounded to float; the inverse uses the conjugate.  Transforms are unnormalised.
