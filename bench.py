@@ -247,7 +247,8 @@ def run_reference(args):
     oracle.build()
     p = oracle.params_of(w)
     probes = w.probes if w.alpha_mrad > 0 else None
-    per_step = max(1, int(args.ref_frames))
+    # one frame per oracle thread (the oracle parallelises over frames), unless set
+    per_step = max(1, int(args.ref_frames)) if args.ref_frames else max(1, oracle.num_threads())
     for _ in range(args.warmup):
         oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
     times = []
@@ -378,7 +379,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-frames", type=int, default=2)
+    ap.add_argument("--ref-frames", type=int, default=0, help="frames per reference step (0: one per host thread)")
     ap.add_argument("--frames", type=int, default=None, help="truncate the trajectory (profiling cases)")
     ap.add_argument("--serving-requests", type=int, default=24, help="requests in the serving run (0: skip)")
     args = ap.parse_args()
