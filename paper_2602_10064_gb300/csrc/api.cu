@@ -502,6 +502,15 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
     ProfScope ps(ctx, "bin", sc.st, (double)nf * A * 28, 0);
     CK(launch_bin(pos, A, nf, S, p.cell[0], p.cell[1], p.cell[2], p.nx, p.ny, slots, recs, offs, nullptr, sc.st));
   }
+  AtomRec* rrecs;
+  int* boffs;
+  const int nyb = ny / SPREAD_YB;
+  CK(sc.get(&rrecs, (size_t)nf * std::max<int64_t>(A, 1)));
+  CK(sc.get(&boffs, (size_t)nf * S * (nyb + 1)));
+  {
+    ProfScope ps(ctx, "sort_rows", sc.st, (double)nf * A * 48 + (double)nf * S * (nyb + 1) * 4, 0);
+    CK(launch_sort_rows(recs, offs, A, nf, S, ny, rrecs, boffs, sc.st));
+  }
   float2 *Bp, *Ap;
   const size_t plane = (size_t)ny * g->band.Wp;
   CK(sc.get(&Bp, (size_t)chunk * sb * g->npair * plane));
@@ -516,8 +525,8 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
       {
         ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
                      (double)nfs * g->npair * ny * fx);
-        CK(launch_splat_row(geo, g->band, recs + (size_t)f0 * A, offs + (size_t)f0 * (S + 1), A, S, s0, sbc, nfs,
-                            g->npair, sk, Bp, sc.st));
+        CK(launch_splat_row(geo, g->band, rrecs + (size_t)f0 * A, boffs + (size_t)f0 * S * (nyb + 1), A, S, s0,
+                            sbc, nfs, g->npair, sk, Bp, sc.st));
       }
       {
         ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
@@ -744,7 +753,8 @@ uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, 
   const RunTiling rt = run_tiling(ctx, p, g, P, F);
   const double chunk = (double)rt.chunk, sb = rt.sb;
   double b = 0;
-  b += (double)F * A * (12 + 16) + (double)F * (S + 1) * 4 + A;     // positions, records, offsets, slots
+  b += (double)F * A * (12 + 16 + 16) + (double)F * (S + 1) * 4 + A;  // positions, records (binned, row-sorted), slots
+  b += (double)F * S * (p.ny / SPREAD_YB + 1) * 4;                      // row-block offsets
   b += chunk * sb * plane * 8 * (g->npair + 2);                      // Bp, Ap, Bt
   b += chunk * sb * nq * 8;                                           // t (or At)
   b += chunk * (double)P * plane * 16;                                // Apsi, Bpsi

@@ -221,6 +221,84 @@ cudaError_t launch_map_slots(const int32_t* Z, int64_t A, const int8_t* lut, int
   return cudaGetLastError();
 }
 
+// One warp per (frame, slice): stable counting sort of the slice's atom records by the grid
+// row of their coordinate, and the offsets of each block of SPREAD_YB rows, so that the
+// spreading pass reads only the atoms whose footprint can reach its rows.  Order within a row
+// is the binning order (atom index), so the spreading sums stay deterministic.
+constexpr int SORT_WARPS = 8;
+__global__ void __launch_bounds__(SORT_WARPS * 32)
+    k_sort_rows(const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S, int nseg, int ny,
+                AtomRec* __restrict__ out, int* __restrict__ boffs) {
+  extern __shared__ int cnt_all[];  // [SORT_WARPS][ny]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = blockIdx.x * SORT_WARPS + warp;
+  if (seg >= nseg) return;  // whole warps; only warp-level barriers below
+  int* cnt = cnt_all + warp * ny;
+  const int f = seg / S, s = seg - f * S;
+  const int lo = offs[(size_t)f * (S + 1) + s], hi = offs[(size_t)f * (S + 1) + s + 1];
+  const AtomRec* R = recs + (size_t)f * A;
+  AtomRec* O = out + (size_t)f * A;
+  const int nyb = ny / SPREAD_YB;
+  int* bo = boffs + (size_t)seg * (nyb + 1);
+  for (int y = lane; y < ny; y += 32) cnt[y] = 0;
+  __syncwarp();
+  for (int j = lo + lane; j < hi; j += 32) atomicAdd(&cnt[R[j].ixy >> 16], 1);
+  __syncwarp();
+  int run = lo;  // exclusive scan over rows; block offsets at multiples of SPREAD_YB
+  for (int y0 = 0; y0 < ny; y0 += 32) {
+    const int y = y0 + lane;
+    const int c = y < ny ? cnt[y] : 0;
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += n;
+    }
+    if (y < ny) {
+      cnt[y] = run + x - c;
+      if (y % SPREAD_YB == 0) bo[y / SPREAD_YB] = run + x - c;
+    }
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) bo[nyb] = hi;
+  __syncwarp();
+  const unsigned below = (1u << lane) - 1u;
+  for (int base = lo; base < hi; base += 32) {  // 32 records at a time, in order: stable
+    const int j = base + lane;
+    const bool valid = j < hi;
+    AtomRec r;
+    int key = -1 - lane;  // distinct for the lanes past the end
+    if (valid) {
+      r = R[j];
+      key = r.ixy >> 16;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    int pos = 0;
+    if (valid && lane == leader) {
+      pos = cnt[key];
+      cnt[key] = pos + __popc(peers);
+    }
+    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & below);
+    if (valid) O[pos] = r;
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_sort_rows(const AtomRec* recs, const int* offs, int64_t A, int64_t nf, int S, int ny,
+                             AtomRec* out, int* boffs, cudaStream_t st) {
+  if (ny % SPREAD_YB != 0 || nf <= 0) return cudaErrorInvalidValue;
+  const int64_t nseg = nf * S;
+  const int smem = SORT_WARPS * ny * (int)sizeof(int);
+  if (smem > 46 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_sort_rows<<<(unsigned)((nseg + SORT_WARPS - 1) / SORT_WARPS), SORT_WARPS * 32, smem, st>>>(
+      recs, offs, (int)A, S, (int)nseg, ny, out, boffs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
                        int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
                        cudaStream_t st) {
@@ -265,11 +343,10 @@ struct SplatSmem {
 
 template <int NX>
 __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::minb(RowCfg<NX>::THREADS))
-    k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ offs, int A, int S,
+    k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ boffs, int A, int S,
                 int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
   constexpr int PL = Tuned<K_SPLAT_ROW, NX>::PLAN;
-  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);                     // FFT scratch (after spreading)
   float2* acc = reinterpret_cast<float2*>(smraw);                    // [G][NX]
@@ -278,53 +355,58 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::m
   float* cfx = phy + NT * G;                                          // [NT] candidate records
   float* cfy = cfx + NT;
   int* cx0 = reinterpret_cast<int*>(cfy + NT);                        // first footprint column
-  int* ciy = cx0 + NT;                                                // iy0 | imag << 16
-  __shared__ int wtot[NW];
+  int* ciy = cx0 + NT;                                                // iy0 | imag << 16, -1: other pair
 
   const int bidx = batch_index();
   if (bidx >= nbatch) return;
   const int pair = bidx % npair, fs = bidx / npair, f = fs / sb, s = s0 + fs % sb;
-  const int tid = threadIdx.x, g = tid / T, t = tid % T, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x, g = tid / T, t = tid % T;
   const int ny = geo.ny, y0 = blockIdx.x * G;
   const int h = sk.half, W2 = 2 * h;
-  const int lo = offs[(size_t)f * (S + 1) + s], hi = offs[(size_t)f * (S + 1) + s + 1];
   const AtomRec* R = recs + (size_t)f * A;
+  // candidates: the atoms of the row blocks covering rows [y0 - h, y0 + G - 2 + h] (their
+  // footprints [iy0 + 1 - h, iy0 + h] meet rows [y0, y0 + G)), at most two contiguous ranges of
+  // the row-sorted slice list (the window may wrap around y = 0)
+  const int nyb = ny / SPREAD_YB;
+  const int* bo = boffs + ((size_t)f * S + s) * (nyb + 1);
+  const int wlo = y0 - h, whi = y0 + G - 2 + h;
+  const int b_lo = wlo >= 0 ? wlo / SPREAD_YB : -((-wlo + SPREAD_YB - 1) / SPREAD_YB), b_hi = whi / SPREAD_YB;
+  int s1, n1, s2 = 0, n2 = 0;
+  if (b_hi - b_lo + 1 >= nyb) {
+    s1 = bo[0];
+    n1 = bo[nyb] - s1;
+  } else if (b_lo < 0) {
+    s1 = bo[b_lo + nyb];
+    n1 = bo[nyb] - s1;
+    s2 = bo[0];
+    n2 = bo[b_hi + 1] - s2;
+  } else if (b_hi >= nyb) {
+    s1 = bo[b_lo];
+    n1 = bo[nyb] - s1;
+    s2 = bo[0];
+    n2 = bo[b_hi - nyb + 1] - s2;
+  } else {
+    s1 = bo[b_lo];
+    n1 = bo[b_hi + 1] - s1;
+  }
+  const int M = n1 + n2;
 
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[g * NX + t + T * e] = make_float2(0.f, 0.f);
 
-  for (int base = lo; base < hi; base += NT) {
-    // 1. stable compaction of the atoms whose footprint meets rows [y0, y0 + G)
+  for (int base = 0; base < M; base += NT) {
+    // 1. the batch's candidate records (atoms of other species pairs are marked and skipped)
     const int j = base + tid;
-    bool cand = false;
-    AtomRec r;
-    if (j < hi) {
-      r = R[j];
+    if (j < M) {
+      const AtomRec r = R[j < n1 ? s1 + j : s2 + (j - n1)];
       const int slot = r.jslot >> 24;
-      if ((slot >> 1) == pair) {
-        const int iy0 = r.ixy >> 16;
-        const int rr = wrap3(iy0 + 1 - h - y0 + 2 * ny, ny);
-        cand = (rr < G) || (rr + W2 - 1 >= ny);
-      }
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, cand);
-    if (lane == 0) wtot[w] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-#pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
-      const int c = wtot[ww];
-      before += (ww < w) ? c : 0;
-      total += c;
-    }
-    if (cand) {
-      const int ci = before + __popc(bal & ((1u << lane) - 1u));
-      cfx[ci] = r.fx;
-      cfy[ci] = r.fy;
-      cx0[ci] = wrap3<NX>((r.ixy & 0xffff) + 1 - h + NX);
-      ciy[ci] = (r.ixy >> 16) | (((r.jslot >> 24) & 1) << 16);
+      cfx[tid] = r.fx;
+      cfy[tid] = r.fy;
+      cx0[tid] = wrap3<NX>((r.ixy & 0xffff) + 1 - h + NX);
+      ciy[tid] = (slot >> 1) == pair ? ((r.ixy >> 16) | ((slot & 1) << 16)) : -1;
     }
     __syncthreads();
+    const int total = M - base < NT ? M - base : NT;
     // 2. kernel tables, one entry per thread: phx[c][d] (d < 2h) and phy[c][g]
     const int per = W2 + G;
     for (int i = tid; i < total * per; i += NT) {
@@ -332,10 +414,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::m
       if (k < W2) {
         phx[c * SPREAD_MAX_W + k] = es_kernel(((float)(k + 1 - h) - cfx[c]) / (float)h, sk.beta);
       } else {
-        const int gg = k - W2;
-        int d = wrap3(y0 + gg - (ciy[c] & 0xffff) + ny, ny);
+        const int gg = k - W2, cy = ciy[c];
+        int d = wrap3(y0 + gg - (cy & 0xffff) + ny, ny);
         if (d > ny / 2) d -= ny;
-        phy[c * G + gg] = (d >= 1 - h && d <= h) ? es_kernel(((float)d - cfy[c]) / (float)h, sk.beta) : 0.f;
+        phy[c * G + gg] = (cy >= 0 && d >= 1 - h && d <= h) ? es_kernel(((float)d - cfy[c]) / (float)h, sk.beta)
+                                                           : 0.f;
       }
     }
     __syncthreads();
@@ -762,7 +845,7 @@ static cudaError_t prep(K kernel, int smem) {
   }
 
 template <int NX>
-static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A,
+static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs, const int* boffs, int64_t A,
                                int S, int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp,
                                cudaStream_t st) {
   if (s0 < 0 || sb < 1 || s0 + sb > S || nfs % sb != 0) return cudaErrorInvalidValue;
@@ -772,12 +855,13 @@ static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs,
   if (e != cudaSuccess) return e;
   const int nb = nfs * npair;
   k_splat_row<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nb), RowCfg<NX>::THREADS, smem, st>>>(
-      g, b, recs, offs, (int)A, S, s0, sb, npair, nb, sk, Bp);
+      g, b, recs, boffs, (int)A, S, s0, sb, npair, nb, sk, Bp);
   return cudaGetLastError();
 }
-cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A, int S,
+cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* boffs, int64_t A, int S,
                              int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
-  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, offs, A, S, s0, sb, nfs, npair, sk, Bp, st);
+  if (g.ny % SPREAD_YB != 0) return cudaErrorInvalidValue;
+  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, boffs, A, S, s0, sb, nfs, npair, sk, Bp, st);
 }
 
 template <int NY>

@@ -69,8 +69,16 @@ cudaError_t launch_map_slots(const int32_t* Z, int64_t A, const int8_t* lut, int
 cudaError_t launch_bin(const float* pos, int64_t A, int64_t nf, int S, double Lx, double Ly, double Lz, int nx,
                        int ny, const int8_t* slot_of_atom, AtomRec* recs, int* offs, int* slice_out,
                        cudaStream_t st);
-// Spreading row pass of slices [s0, s0 + sb) of nfs / sb frames (batch = (frame, slice, pair)).
-cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* offs, int64_t A, int S,
+// Grid rows per block of the row-sorted atom lists of the spreading pass (divides every grid length).
+constexpr int SPREAD_YB = 8;
+// Row-sorted copy of the binned records: per (frame, slice) a stable sort by grid row, and the
+// offsets of each block of SPREAD_YB rows, boffs [nf][S][ny / SPREAD_YB + 1] (absolute within
+// the frame).
+cudaError_t launch_sort_rows(const AtomRec* recs, const int* offs, int64_t A, int64_t nf, int S, int ny,
+                             AtomRec* out, int* boffs, cudaStream_t st);
+// Spreading row pass of slices [s0, s0 + sb) of nfs / sb frames (batch = (frame, slice, pair)),
+// from the row-sorted records and their row-block offsets.
+cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* boffs, int64_t A, int S,
                              int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st);
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                            float2* Ap, cudaStream_t st);
