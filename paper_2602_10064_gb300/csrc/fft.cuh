@@ -146,50 +146,69 @@ __device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
   a2 = m - h * d;
 }
 
-// exp(SIGN 2 pi i j / 12) for the small j a radix-12 butterfly needs.
+// exp(SIGN 2 pi i j / 24) (j compile-time after unrolling): the twiddles inside the radix-6,
+// 12 and 24 butterflies.
 template <int SIGN>
-__device__ __forceinline__ float2 w12(int j) {
-  const float h = 0.86602540378443865f;
+__device__ __forceinline__ float2 w24(int j) {
+  const float c15 = 0.96592582628906829f, s15 = 0.25881904510252076f, h = 0.86602540378443865f,
+              r2 = 0.70710678118654752f;
   float c, s;
-  switch (j % 12) {
+  switch (j % 24) {
     case 0: c = 1.f; s = 0.f; break;
-    case 1: c = h; s = 0.5f; break;
-    case 2: c = 0.5f; s = h; break;
-    case 3: c = 0.f; s = 1.f; break;
-    case 4: c = -0.5f; s = h; break;
-    case 5: c = -h; s = 0.5f; break;
-    case 6: c = -1.f; s = 0.f; break;
-    case 7: c = -h; s = -0.5f; break;
-    case 8: c = -0.5f; s = -h; break;
-    case 9: c = 0.f; s = -1.f; break;
-    case 10: c = 0.5f; s = -h; break;
-    default: c = h; s = -0.5f; break;
+    case 1: c = c15; s = s15; break;
+    case 2: c = h; s = 0.5f; break;
+    case 3: c = r2; s = r2; break;
+    case 4: c = 0.5f; s = h; break;
+    case 5: c = s15; s = c15; break;
+    case 6: c = 0.f; s = 1.f; break;
+    case 7: c = -s15; s = c15; break;
+    case 8: c = -0.5f; s = h; break;
+    case 9: c = -r2; s = r2; break;
+    case 10: c = -h; s = 0.5f; break;
+    case 11: c = -c15; s = s15; break;
+    case 12: c = -1.f; s = 0.f; break;
+    case 13: c = -c15; s = -s15; break;
+    case 14: c = -h; s = -0.5f; break;
+    case 15: c = -r2; s = -r2; break;
+    case 16: c = -0.5f; s = -h; break;
+    case 17: c = -s15; s = -c15; break;
+    case 18: c = 0.f; s = -1.f; break;
+    case 19: c = s15; s = -c15; break;
+    case 20: c = 0.5f; s = -h; break;
+    case 21: c = r2; s = -r2; break;
+    case 22: c = h; s = -0.5f; break;
+    default: c = c15; s = -s15; break;
   }
   return make_float2(c, SIGN < 0 ? -s : s);
 }
 
-// Radix-12 as 4 x 3: radix-4 over n1 (stride 3), twiddle w12^(n2 k1), radix-3 over n2.
-template <int SIGN>
-__device__ __forceinline__ void dft12(float2* u) {
-  float2 y[3][4];
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_r(float2* u);
+
+// Radix R1 * R2 (a divisor of 24) as R1 x R2: radix-R1 over n1 (stride R2), twiddle
+// w_R^(n2 k1), radix-R2 over n2; natural order in and out.
+template <int R1, int R2, int SIGN>
+__device__ __forceinline__ void dft_ct(float2* u) {
+  constexpr int R = R1 * R2;
+  static_assert(24 % R == 0, "twiddles of dft_ct come from the 24-point table");
+  float2 y[R2][R1];
 #pragma unroll
-  for (int n2 = 0; n2 < 3; ++n2) {
-    y[n2][0] = u[n2];
-    y[n2][1] = u[3 + n2];
-    y[n2][2] = u[6 + n2];
-    y[n2][3] = u[9 + n2];
-    dft4<SIGN>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+  for (int n2 = 0; n2 < R2; ++n2) {
 #pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1)
-      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w12<SIGN>(n2 * k1));
+    for (int n1 = 0; n1 < R1; ++n1) y[n2][n1] = u[n2 + R2 * n1];
+    dft_r<R1, SIGN>(y[n2]);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1)
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w24<SIGN>((24 / R) * n2 * k1));
   }
 #pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) {
-    float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1];
-    dft3<SIGN>(a0, a1, a2);
-    u[k1] = a0;
-    u[k1 + 4] = a1;
-    u[k1 + 8] = a2;
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 z[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) z[n2] = y[n2][k1];
+    dft_r<R2, SIGN>(z);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) u[k1 + R1 * k2] = z[k2];
   }
 }
 
@@ -198,8 +217,10 @@ __device__ __forceinline__ void dft_r(float2* u) {
   if constexpr (R == 2) dft2<SIGN>(u);
   else if constexpr (R == 3) dft3<SIGN>(u[0], u[1], u[2]);
   else if constexpr (R == 4) dft4<SIGN>(u);
+  else if constexpr (R == 6) dft_ct<2, 3, SIGN>(u);
   else if constexpr (R == 8) dft8<SIGN>(u);
-  else if constexpr (R == 12) dft12<SIGN>(u);
+  else if constexpr (R == 12) dft_ct<4, 3, SIGN>(u);
+  else if constexpr (R == 24) dft_ct<8, 3, SIGN>(u);
   else dft16<SIGN>(u);
 }
 
@@ -207,11 +228,11 @@ __device__ __forceinline__ void dft_r(float2* u) {
 __host__ __device__ constexpr bool fft_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Elements per thread (E) for a transform of length N: 8 or 16 for powers of two (8 for
-// N <= 64), 12 for the lengths with a factor 3.  A kernel picks E per pass direction (powers
-// of two); T = N / E threads share one transform.
+// N <= 64), 24 for 768 and 1152 (three passes), 12 for the other lengths with a factor 3.  A
+// kernel picks E per pass direction (powers of two); T = N / E threads share one transform.
 template <int N, int EPREF>
 struct FftPlan {
-  static constexpr int E = !fft_pow2(N) ? 12 : ((N <= 64) ? 8 : EPREF);
+  static constexpr int E = fft_pow2(N) ? ((N <= 64) ? 8 : EPREF) : ((N == 768 || N == 1152) ? 24 : 12);
   static constexpr int T = N / E;
 };
 
@@ -367,16 +388,14 @@ __device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const Idx& idx, 
     fft_pass<384, E, 4, 12, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<384, E, 4, 48, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<384, E, 2, 192, SIGN, true>(v, sm, idx, t, tw, sync);
-  } else if constexpr (E == 12 && N == 768) {
-    fft_pass<768, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<768, E, 4, 12, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<768, E, 4, 48, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<768, E, 4, 192, SIGN, true>(v, sm, idx, t, tw, sync);
-  } else if constexpr (E == 12 && N == 1152) {
-    fft_pass<1152, E, 12, 1, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1152, E, 12, 12, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1152, E, 4, 144, SIGN, false>(v, sm, idx, t, tw, sync);
-    fft_pass<1152, E, 2, 576, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 24 && N == 768) {
+    fft_pass<768, E, 24, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<768, E, 4, 24, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<768, E, 8, 96, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 24 && N == 1152) {
+    fft_pass<1152, E, 24, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1152, E, 6, 24, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1152, E, 8, 144, SIGN, true>(v, sm, idx, t, tw, sync);
   } else {
     static_assert(N == 32, "unsupported FFT length");
   }

@@ -40,9 +40,10 @@ struct Tuned {
   static constexpr bool COLUMN = K == K_COL_POT || K == K_COL_T || K == K_PROBE_COL || K == K_SLICE_COL;
   static constexpr int PLAN = V & 1;
   static constexpr int WIDE = (COLUMN && (V & 4)) ? 1 : 0;
-  // resident CTAs per SM requested for a CTA of `threads`: 512 (variant & 2: 768) threads per SM
-  static constexpr int minb(int threads) {
-    return ((V & 2) ? 768 : 512) / threads > 1 ? ((V & 2) ? 768 : 512) / threads : 1;
+  // resident CTAs per SM requested for a CTA of `threads`: `target` threads per SM (variant & 2:
+  // 1.5 times as many)
+  __host__ __device__ static constexpr int minb(int threads, int target) {
+    return ((V & 2) ? target * 3 / 2 : target) / threads > 1 ? ((V & 2) ? target * 3 / 2 : target) / threads : 1;
   }
 };
 
@@ -54,14 +55,25 @@ struct Tuned {
 #define TACAW_COL_E 16
 #endif
 
+// Largest power of two <= x (x >= 1).
+__host__ __device__ constexpr int floor_pow2(int x) {
+  int p = 1;
+  while (2 * p <= x) p *= 2;
+  return p;
+}
+
+// Row passes: G rows per CTA, one transform group of T threads per row.  Transforms of 24
+// elements per thread need about 170 registers, so those CTAs are smaller and the SM holds
+// 384 instead of 512 threads (TARGET).
 template <int N>
 struct RowCfg {
   static constexpr int E = FftPlan<N, TACAW_ROW_E>::E;
   static constexpr int T = N / E;
-  static constexpr int G = (256 / T) > 32 ? 32 : ((256 / T) < 1 ? 1 : 256 / T);  // rows per CTA
-  static constexpr int THREADS = G * T;  // one transform group of T threads per row
+  static constexpr int TARGET = E >= 24 ? 384 : 512;
+  static constexpr int G0 = (TARGET / 2) / T;
+  static constexpr int G = G0 > 32 ? 32 : (G0 < 1 ? 1 : floor_pow2(G0));  // rows per CTA
+  static constexpr int THREADS = G * T;
   static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
-  static_assert(T <= 32 || T % 32 == 0, "a row group larger than a warp must be whole warps");
 };
 
 // Column passes: C columns per CTA (about 256 threads; WIDE doubles C, about 512 threads).
@@ -69,15 +81,29 @@ template <int N, int WIDE = 0>
 struct ColCfg {
   static constexpr int E = FftPlan<N, TACAW_COL_E>::E;
   static constexpr int T = N / E;
-  static constexpr int C0 = (256 << WIDE) / T;
-  static constexpr int C = C0 > 32 ? 32 : (C0 < 4 ? 4 : C0);  // columns per CTA
+  static constexpr int TARGET = E >= 24 ? 384 : 512;
+  static constexpr int C0 = ((TARGET / 2) << WIDE) / T;
+  static constexpr int C = C0 > 32 ? 32 : (C0 < 4 ? 4 : floor_pow2(C0));  // columns per CTA (divides Wp)
   static constexpr int THREADS = C * T;
   static constexpr int SMEM = N * C * (int)sizeof(float2);
 };
 
+// Resident CTAs per SM requested from the compiler for kernel K's row or column pass.
+template <int K, int N>
+__host__ __device__ constexpr int row_minb() {
+  return Tuned<K, N>::minb(RowCfg<N>::THREADS, RowCfg<N>::TARGET);
+}
+template <int K, int N>
+__host__ __device__ constexpr int col_minb() {
+  return Tuned<K, N>::minb(ColCfg<N, Tuned<K, N>::WIDE>::THREADS, ColCfg<N, Tuned<K, N>::WIDE>::TARGET);
+}
+
+// Barrier of one row transform: the group's own (warp, or named barrier over whole warps), or
+// the CTA barrier when a group of T threads is not made of whole warps (T = 48: 1152 points).
 template <int T>
-__device__ __forceinline__ GroupSync<T> group_sync(int g) {
-  return GroupSync<T>{1 + g};
+__device__ __forceinline__ auto group_sync(int g) {
+  if constexpr (T <= 32 || T % 32 == 0) return GroupSync<T>{1 + g};
+  else return BlockSync{};
 }
 
 // Batch index over (grid.y, grid.z); batches beyond nb return before any barrier.
@@ -342,7 +368,7 @@ struct SplatSmem {
 };
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::minb(RowCfg<NX>::THREADS))
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SPLAT_ROW, NX>())
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ boffs, int A, int S,
                 int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
@@ -452,7 +478,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SPLAT_ROW, NX>::m
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
 template <int NY, bool ONE>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREADS,
-                                  Tuned<K_COL_POT, NY>::minb(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREADS))
+                                  col_minb<K_COL_POT, NY>())
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
   using CC = ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>;
@@ -466,7 +492,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREAD
   const ColIdx<C> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
-  if (ONE) {
+  if constexpr (ONE) {
     // one species pair: no accumulator held across the transforms
     const float2* src = Bp + (size_t)fs * NY * b.Wp + cc;
     float2 v[E];
@@ -480,31 +506,31 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREAD
     float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
 #pragma unroll
     for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
-    return;
+  } else {
+    float2 acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = make_float2(0.f, 0.f);
+    for (int pr = 0; pr < npair; ++pr) {
+      const float2* src = Bp + (size_t)(fs * npair + pr) * NY * b.Wp + cc;
+      float2 v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+      fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
+      const float2* m = mtab + (size_t)pr * NY * b.Wp + cc;
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
+    }
+    fft<NY, +1, PL>(acc, sm, idx, t, tw, sync);
+    float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
+#pragma unroll
+    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = acc[e];
   }
-  float2 acc[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) acc[e] = make_float2(0.f, 0.f);
-  for (int pr = 0; pr < npair; ++pr) {
-    const float2* src = Bp + (size_t)(fs * npair + pr) * NY * b.Wp + cc;
-    float2 v[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
-    fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
-    const float2* m = mtab + (size_t)pr * NY * b.Wp + cc;
-#pragma unroll
-    for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
-  }
-  fft<NY, +1, PL>(acc, sm, idx, t, tw, sync);
-  float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
-#pragma unroll
-  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = acc[e];
 }
 
 // Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
 // t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>::minb(RowCfg<NX>::THREADS))
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_POT_OUT, NX>())
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
@@ -544,7 +570,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_POT_OUT, NX>:
 // a3: transmission from a stored V.
 // ============================================================================================
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::minb(RowCfg<NX>::THREADS))
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_VT, NX>())
     k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
              float2* __restrict__ out) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
@@ -575,7 +601,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_VT, NX>::minb
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
-                                  Tuned<K_COL_T, NY>::minb(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS))
+                                  col_minb<K_COL_T, NY>())
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
   using CC = ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
@@ -607,7 +633,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
 
 // Row pass out of the band limit: IFFT_x -> t (full row).
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::minb(RowCfg<NX>::THREADS))
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_TOUT, NX>())
     k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   constexpr int PL = Tuned<K_ROW_TOUT, NX>::PLAN;
@@ -630,7 +656,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_ROW_TOUT, NX>::mi
 // ============================================================================================
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THREADS,
-                                  Tuned<K_PROBE_COL, NY>::minb(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THREADS))
+                                  col_minb<K_PROBE_COL, NY>())
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey,
                 const float2* __restrict__ chi, int P, float amp, float2* __restrict__ Bpr) {
   using CC = ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>;
@@ -657,7 +683,7 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THRE
 }
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_PROBE_ROW, NX>::minb(RowCfg<NX>::THREADS))
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_PROBE_ROW, NX>())
     k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
   constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
   constexpr int PL = Tuned<K_PROBE_ROW, NX>::PLAN;
@@ -687,7 +713,7 @@ struct SliceRowSmem {
 };
 
 template <int NX, bool FIRST, bool PLANE, bool TF>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::minb(RowCfg<NX>::THREADS))
+__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SLICE_ROW, NX>())
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
                 float2* __restrict__ Bpsi) {
@@ -741,7 +767,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, Tuned<K_SLICE_ROW, NX>::m
 
 template <int NY, bool LAST>
 __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THREADS,
-                                  Tuned<K_SLICE_COL, NY>::minb(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THREADS))
+                                  col_minb<K_SLICE_COL, NY>())
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
