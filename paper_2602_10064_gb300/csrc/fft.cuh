@@ -185,6 +185,49 @@ __device__ __forceinline__ float2 w24(int j) {
 template <int R, int SIGN>
 __device__ __forceinline__ void dft_r(float2* u);
 
+// exp(SIGN 2 pi i j / 32) for j = n2 k1 < 32 (compile-time after unrolling).
+template <int SIGN>
+__device__ __forceinline__ float2 w32(int j) {
+  // cos(2 pi m / 32) for m = 0 .. 8
+  const float c[9] = {1.f, 0.98078528040323044f, 0.92387953251128674f, 0.83146961230254524f,
+                      0.70710678118654752f, 0.55557023301960218f, 0.38268343236508978f, 0.19509032201612826f,
+                      0.f};
+  const int m = j & 31, q = m >> 3, r = m & 7;  // angle = q * 90 deg + r * 11.25 deg
+  float cs = c[r], sn = c[8 - r];               // cos, sin of r * 11.25 deg
+  float x, y;
+  switch (q) {
+    case 0: x = cs; y = sn; break;
+    case 1: x = -sn; y = cs; break;
+    case 2: x = -cs; y = -sn; break;
+    default: x = sn; y = -cs; break;
+  }
+  return make_float2(x, SIGN < 0 ? -y : y);
+}
+
+// Radix-32 as 8 x 4: radix-8 over n1 (stride 4), twiddle w32^(n2 k1), radix-4 over n2.
+template <int SIGN>
+__device__ __forceinline__ void dft32(float2* u) {
+  float2 y[4][8];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) y[n2][n1] = u[n2 + 4 * n1];
+    dft8<SIGN>(y[n2]);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1)
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w32<SIGN>(n2 * k1));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1], a3 = y[3][k1];
+    dft4<SIGN>(a0, a1, a2, a3);
+    u[k1] = a0;
+    u[k1 + 8] = a1;
+    u[k1 + 16] = a2;
+    u[k1 + 24] = a3;
+  }
+}
+
 // Radix R1 * R2 (a divisor of 24) as R1 x R2: radix-R1 over n1 (stride R2), twiddle
 // w_R^(n2 k1), radix-R2 over n2; natural order in and out.
 template <int R1, int R2, int SIGN>
@@ -221,6 +264,7 @@ __device__ __forceinline__ void dft_r(float2* u) {
   else if constexpr (R == 8) dft8<SIGN>(u);
   else if constexpr (R == 12) dft_ct<4, 3, SIGN>(u);
   else if constexpr (R == 24) dft_ct<8, 3, SIGN>(u);
+  else if constexpr (R == 32) dft32<SIGN>(u);
   else dft16<SIGN>(u);
 }
 
@@ -332,6 +376,18 @@ __device__ __forceinline__ void fft(float2 (&v)[E], float2* sm, const Idx& idx, 
   } else if constexpr (N == 64) {
     fft_pass<64, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<64, E, 8, 8, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 32 && N == 128) {
+    fft_pass<128, E, 32, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<128, E, 4, 32, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 32 && N == 256) {
+    fft_pass<256, E, 32, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<256, E, 8, 32, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 32 && N == 512) {
+    fft_pass<512, E, 32, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<512, E, 16, 32, SIGN, true>(v, sm, idx, t, tw, sync);
+  } else if constexpr (E == 32 && N == 1024) {
+    fft_pass<1024, E, 32, 1, SIGN, false>(v, sm, idx, t, tw, sync);
+    fft_pass<1024, E, 32, 32, SIGN, true>(v, sm, idx, t, tw, sync);
   } else if constexpr (E == 8 && N == 128) {
     fft_pass<128, E, 8, 1, SIGN, false>(v, sm, idx, t, tw, sync);
     fft_pass<128, E, 4, 8, SIGN, false>(v, sm, idx, t, tw, sync);

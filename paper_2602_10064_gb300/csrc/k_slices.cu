@@ -19,11 +19,12 @@ namespace tacaw {
 
 // Per-kernel variants of the FFT pass kernels, chosen per transform length by the autotuner
 // (paper_2602_10064_gb300/tune.py), which times every variant on GB300 and writes
-// tuning_table.h.  Variant bits: 1 = radix-8 plans (512 and 1024 points), 2 = three resident
-// CTAs per SM (register cap 80) instead of two (128), 4 = column passes only: twice the
-// columns per CTA (one CTA of about 512 threads per SM, register cap 128), so that each load
-// instruction covers whole 128-byte lines.  TACAW_TUNE_FORCE=v builds every kernel as variant
-// v (the tuner's measurement builds).
+// tuning_table.h.  Variant bits: 1 = radix-8 plans (512 and 1024 points, 16 elements per
+// thread), 2 = 1.5 times as many resident threads per SM (fewer registers each), 4 = column
+// passes only: twice the columns per CTA, so that each load instruction covers whole 128-byte
+// lines, 8 = 32 elements per thread for the powers of two from 128 points (two-pass
+// transforms, about 170 registers).  TACAW_TUNE_FORCE=v builds every kernel as variant v (the
+// tuner's measurement builds).
 enum KernelId {
   K_SPLAT_ROW, K_COL_POT, K_ROW_POT_OUT, K_ROW_VT, K_COL_T, K_ROW_TOUT, K_PROBE_COL, K_PROBE_ROW,
   K_SLICE_ROW, K_SLICE_COL
@@ -38,7 +39,8 @@ template <int K, int N>
 struct Tuned {
   static constexpr int V = TACAW_TUNE_FORCE >= 0 ? TACAW_TUNE_FORCE : tuned_variant(K, N);
   static constexpr bool COLUMN = K == K_COL_POT || K == K_COL_T || K == K_PROBE_COL || K == K_SLICE_COL;
-  static constexpr int PLAN = V & 1;
+  static constexpr int EV = (V & 8) ? 1 : 0;
+  static constexpr int PLAN = (V & 1) && !EV;
   static constexpr int WIDE = (COLUMN && (V & 4)) ? 1 : 0;
   // resident CTAs per SM requested for a CTA of `threads`: `target` threads per SM (variant & 2:
   // 1.5 times as many)
@@ -65,9 +67,10 @@ __host__ __device__ constexpr int floor_pow2(int x) {
 // Row passes: G rows per CTA, one transform group of T threads per row.  Transforms of 24
 // elements per thread need about 170 registers, so those CTAs are smaller and the SM holds
 // 384 instead of 512 threads (TARGET).
-template <int N>
+// EV = 1: 32 elements per thread (two-pass transforms) for the powers of two from 128 points.
+template <int N, int EV = 0>
 struct RowCfg {
-  static constexpr int E = FftPlan<N, TACAW_ROW_E>::E;
+  static constexpr int E = (EV && fft_pow2(N) && N >= 128) ? 32 : FftPlan<N, TACAW_ROW_E>::E;
   static constexpr int T = N / E;
   static constexpr int TARGET = E >= 24 ? 384 : 512;
   static constexpr int G0 = (TARGET / 2) / T;
@@ -77,9 +80,9 @@ struct RowCfg {
 };
 
 // Column passes: C columns per CTA (about 256 threads; WIDE doubles C, about 512 threads).
-template <int N, int WIDE = 0>
+template <int N, int WIDE = 0, int EV = 0>
 struct ColCfg {
-  static constexpr int E = FftPlan<N, TACAW_COL_E>::E;
+  static constexpr int E = (EV && fft_pow2(N) && N >= 128) ? 32 : FftPlan<N, TACAW_COL_E>::E;
   static constexpr int T = N / E;
   static constexpr int TARGET = E >= 24 ? 384 : 512;
   static constexpr int C0 = ((TARGET / 2) << WIDE) / T;
@@ -88,14 +91,22 @@ struct ColCfg {
   static constexpr int SMEM = N * C * (int)sizeof(float2);
 };
 
-// Resident CTAs per SM requested from the compiler for kernel K's row or column pass.
-template <int K, int N>
-__host__ __device__ constexpr int row_minb() {
-  return Tuned<K, N>::minb(RowCfg<N>::THREADS, RowCfg<N>::TARGET);
-}
-template <int K, int N>
-__host__ __device__ constexpr int col_minb() {
-  return Tuned<K, N>::minb(ColCfg<N, Tuned<K, N>::WIDE>::THREADS, ColCfg<N, Tuned<K, N>::WIDE>::TARGET);
+// The configuration of each pass kernel; a kernel and its launcher name the same alias.
+template <int N> using SplatCfg = RowCfg<N, Tuned<K_SPLAT_ROW, N>::EV>;
+template <int N> using PotOutCfg = RowCfg<N, Tuned<K_ROW_POT_OUT, N>::EV>;
+template <int N> using RowVtCfg = RowCfg<N, Tuned<K_ROW_VT, N>::EV>;
+template <int N> using RowToutCfg = RowCfg<N, Tuned<K_ROW_TOUT, N>::EV>;
+template <int N> using ProbeRowCfg = RowCfg<N, Tuned<K_PROBE_ROW, N>::EV>;
+template <int N> using SliceRowCfg = RowCfg<N, Tuned<K_SLICE_ROW, N>::EV>;
+template <int N> using ColPotCfg = ColCfg<N, Tuned<K_COL_POT, N>::WIDE, Tuned<K_COL_POT, N>::EV>;
+template <int N> using ColTCfg = ColCfg<N, Tuned<K_COL_T, N>::WIDE, Tuned<K_COL_T, N>::EV>;
+template <int N> using ProbeColCfg = ColCfg<N, Tuned<K_PROBE_COL, N>::WIDE, Tuned<K_PROBE_COL, N>::EV>;
+template <int N> using SliceColCfg = ColCfg<N, Tuned<K_SLICE_COL, N>::WIDE, Tuned<K_SLICE_COL, N>::EV>;
+
+// Resident CTAs per SM requested from the compiler for kernel K with configuration Cfg.
+template <int K, int N, class Cfg>
+__host__ __device__ constexpr int minb_of() {
+  return Tuned<K, N>::minb(Cfg::THREADS, Cfg::TARGET);
 }
 
 // Barrier of one row transform: the group's own (warp, or named barrier over whole warps), or
@@ -361,17 +372,17 @@ constexpr int SPREAD_MAX_W = 16;
 // thread, so the sums are race-free and in candidate order), then the candidate tables.
 template <int NX>
 struct SplatSmem {
-  static constexpr int NT = RowCfg<NX>::THREADS, G = RowCfg<NX>::G;
+  static constexpr int NT = SplatCfg<NX>::THREADS, G = SplatCfg<NX>::G;
   static constexpr int ACC = G * NX * 8;
   static constexpr int TAB = NT * (SPREAD_MAX_W + G) * 4 + NT * 4 * 4;
-  static constexpr int BYTES = (ACC + TAB) > RowCfg<NX>::SMEM ? (ACC + TAB) : RowCfg<NX>::SMEM;
+  static constexpr int BYTES = (ACC + TAB) > SplatCfg<NX>::SMEM ? (ACC + TAB) : SplatCfg<NX>::SMEM;
 };
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SPLAT_ROW, NX>())
+__global__ void __launch_bounds__(SplatCfg<NX>::THREADS, minb_of<K_SPLAT_ROW, NX, SplatCfg<NX>>())
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ boffs, int A, int S,
                 int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
-  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G, NT = RowCfg<NX>::THREADS;
+  constexpr int E = SplatCfg<NX>::E, T = SplatCfg<NX>::T, G = SplatCfg<NX>::G, NT = SplatCfg<NX>::THREADS;
   constexpr int PL = Tuned<K_SPLAT_ROW, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);                     // FFT scratch (after spreading)
@@ -477,11 +488,10 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SPLAT_ROW, NX>
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
 template <int NY, bool ONE>
-__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREADS,
-                                  col_minb<K_COL_POT, NY>())
+__global__ void __launch_bounds__(ColPotCfg<NY>::THREADS, minb_of<K_COL_POT, NY, ColPotCfg<NY>>())
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
-  using CC = ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>;
+  using CC = ColPotCfg<NY>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_COL_POT, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -530,10 +540,10 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>::THREAD
 // Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
 // t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_POT_OUT, NX>())
+__global__ void __launch_bounds__(PotOutCfg<NX>::THREADS, minb_of<K_ROW_POT_OUT, NX, PotOutCfg<NX>>())
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
-  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = PotOutCfg<NX>::E, T = PotOutCfg<NX>::T, G = PotOutCfg<NX>::G;
   constexpr int PL = Tuned<K_ROW_POT_OUT, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -570,10 +580,10 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_POT_OUT, N
 // a3: transmission from a stored V.
 // ============================================================================================
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_VT, NX>())
+__global__ void __launch_bounds__(RowVtCfg<NX>::THREADS, minb_of<K_ROW_VT, NX, RowVtCfg<NX>>())
     k_row_vt(Geo geo, Band b, const float* __restrict__ V, int nbatch, int bandlimit, float sigma,
              float2* __restrict__ out) {
-  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowVtCfg<NX>::E, T = RowVtCfg<NX>::T, G = RowVtCfg<NX>::G;
   constexpr int PL = Tuned<K_ROW_VT, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -600,10 +610,9 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_VT, NX>())
 
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
-                                  col_minb<K_COL_T, NY>())
+__global__ void __launch_bounds__(ColTCfg<NY>::THREADS, minb_of<K_COL_T, NY, ColTCfg<NY>>())
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
-  using CC = ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>;
+  using CC = ColTCfg<NY>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_COL_T, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -633,9 +642,9 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>::THREADS,
 
 // Row pass out of the band limit: IFFT_x -> t (full row).
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_TOUT, NX>())
+__global__ void __launch_bounds__(RowToutCfg<NX>::THREADS, minb_of<K_ROW_TOUT, NX, RowToutCfg<NX>>())
     k_row_tout(Geo geo, Band b, const float2* __restrict__ At, int nbatch, float2* __restrict__ tout) {
-  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = RowToutCfg<NX>::E, T = RowToutCfg<NX>::T, G = RowToutCfg<NX>::G;
   constexpr int PL = Tuned<K_ROW_TOUT, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -655,11 +664,10 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_ROW_TOUT, NX>(
 // Probe: psi0(k) = A(k) exp(-2 pi i k.r_p) amp, then a unitary inverse transform.
 // ============================================================================================
 template <int NY>
-__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THREADS,
-                                  col_minb<K_PROBE_COL, NY>())
+__global__ void __launch_bounds__(ProbeColCfg<NY>::THREADS, minb_of<K_PROBE_COL, NY, ProbeColCfg<NY>>())
     k_probe_col(Geo geo, Band ap, const float2* __restrict__ ex, const float2* __restrict__ ey,
                 const float2* __restrict__ chi, int P, float amp, float2* __restrict__ Bpr) {
-  using CC = ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>;
+  using CC = ProbeColCfg<NY>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_PROBE_COL, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -683,9 +691,9 @@ __global__ void __launch_bounds__(ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>::THRE
 }
 
 template <int NX>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_PROBE_ROW, NX>())
+__global__ void __launch_bounds__(ProbeRowCfg<NX>::THREADS, minb_of<K_PROBE_ROW, NX, ProbeRowCfg<NX>>())
     k_probe_row(Geo geo, Band ap, const float2* __restrict__ Bpr, int P, float scale, float2* __restrict__ psi0) {
-  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = ProbeRowCfg<NX>::E, T = ProbeRowCfg<NX>::T, G = ProbeRowCfg<NX>::G;
   constexpr int PL = Tuned<K_PROBE_ROW, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -709,15 +717,15 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_PROBE_ROW, NX>
 // Shared memory of the slice row pass: the FFT scratch, plus (TF) one stashed t row per group.
 template <int NX, bool TF>
 struct SliceRowSmem {
-  static constexpr int BYTES = RowCfg<NX>::SMEM + (TF ? RowCfg<NX>::G * NX * (int)sizeof(float2) : 0);
+  static constexpr int BYTES = SliceRowCfg<NX>::SMEM + (TF ? SliceRowCfg<NX>::G * NX * (int)sizeof(float2) : 0);
 };
 
 template <int NX, bool FIRST, bool PLANE, bool TF>
-__global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SLICE_ROW, NX>())
+__global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW, NX, SliceRowCfg<NX>>())
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
                 float2* __restrict__ Bpsi) {
-  constexpr int E = RowCfg<NX>::E, T = RowCfg<NX>::T, G = RowCfg<NX>::G;
+  constexpr int E = SliceRowCfg<NX>::E, T = SliceRowCfg<NX>::T, G = SliceRowCfg<NX>::G;
   constexpr int PL = Tuned<K_SLICE_ROW, NX>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -738,7 +746,7 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SLICE_ROW, NX>
   }
   // TF: inverse-transform t first and stash the row (each thread rereads only its own
   // positions, so no barrier is needed); only one row of the wave is then live in registers
-  float2* tst = reinterpret_cast<float2*>(smraw + RowCfg<NX>::SMEM) + g * NX;
+  float2* tst = reinterpret_cast<float2*>(smraw + SliceRowCfg<NX>::SMEM) + g * NX;
   if (TF) {
     load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
     fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
@@ -766,12 +774,11 @@ __global__ void __launch_bounds__(RowCfg<NX>::THREADS, row_minb<K_SLICE_ROW, NX>
 }
 
 template <int NY, bool LAST>
-__global__ void __launch_bounds__(ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>::THREADS,
-                                  col_minb<K_SLICE_COL, NY>())
+__global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL, NY, SliceColCfg<NY>>())
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
                 float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
-  using CC = ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>;
+  using CC = SliceColCfg<NY>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_SLICE_COL, NY>::PLAN;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -880,7 +887,7 @@ static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs,
   cudaError_t e = prep(k_splat_row<NX>, smem);
   if (e != cudaSuccess) return e;
   const int nb = nfs * npair;
-  k_splat_row<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nb), RowCfg<NX>::THREADS, smem, st>>>(
+  k_splat_row<NX><<<batch_grid(g.ny / SplatCfg<NX>::G, nb), SplatCfg<NX>::THREADS, smem, st>>>(
       g, b, recs, boffs, (int)A, S, s0, sb, npair, nb, sk, Bp);
   return cudaGetLastError();
 }
@@ -893,7 +900,7 @@ cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, c
 template <int NY>
 static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                              float2* Ap, cudaStream_t st) {
-  using CC = ColCfg<NY, Tuned<K_COL_POT, NY>::WIDE>;
+  using CC = ColPotCfg<NY>;
   const dim3 grid = batch_grid(b.Wp / CC::C, nfs);
   cudaError_t e;
   if (npair == 1) {
@@ -913,7 +920,7 @@ cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const 
 template <int NX>
 static cudaError_t row_pot_out_n(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
                                  float* V, float2* out, cudaStream_t st) {
-  k_row_pot_out<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nfs), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(
+  k_row_pot_out<NX><<<batch_grid(g.ny / PotOutCfg<NX>::G, nfs), PotOutCfg<NX>::THREADS, PotOutCfg<NX>::SMEM, st>>>(
       g, b, Ap, nfs, mode, sigma, V, out);
   return cudaGetLastError();
 }
@@ -925,7 +932,7 @@ cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, in
 template <int NX>
 static cudaError_t row_vt_n(const Geo& g, const Band& b, const float* V, int nfs, int bl, float sigma, float2* out,
                             cudaStream_t st) {
-  k_row_vt<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nfs), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(
+  k_row_vt<NX><<<batch_grid(g.ny / RowVtCfg<NX>::G, nfs), RowVtCfg<NX>::THREADS, RowVtCfg<NX>::SMEM, st>>>(
       g, b, V, nfs, bl, sigma, out);
   return cudaGetLastError();
 }
@@ -937,7 +944,7 @@ cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, 
 template <int NY>
 static cudaError_t col_t_n(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
                            cudaStream_t st) {
-  using CC = ColCfg<NY, Tuned<K_COL_T, NY>::WIDE>;
+  using CC = ColTCfg<NY>;
   const cudaError_t e = prep(k_col_t<NY>, CC::SMEM);
   if (e != cudaSuccess) return e;
   k_col_t<NY><<<batch_grid(b.Wp / CC::C, nfs), CC::THREADS, CC::SMEM, st>>>(g, b, Bt, nfs,
@@ -951,8 +958,8 @@ cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs,
 
 template <int NX>
 static cudaError_t row_tout_n(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st) {
-  k_row_tout<NX><<<batch_grid(g.ny / RowCfg<NX>::G, nfs), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(g, b, At,
-                                                                                                      nfs, t);
+  using RC = RowToutCfg<NX>;
+  k_row_tout<NX><<<batch_grid(g.ny / RC::G, nfs), RC::THREADS, RC::SMEM, st>>>(g, b, At, nfs, t);
   return cudaGetLastError();
 }
 cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st) {
@@ -962,7 +969,7 @@ cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int n
 template <int NY>
 static cudaError_t probe_col_n(const Geo& g, const Band& ap, const float2* ex, const float2* ey, const float2* chi,
                                int P, float amp, float2* Bpr, cudaStream_t st) {
-  using CC = ColCfg<NY, Tuned<K_PROBE_COL, NY>::WIDE>;
+  using CC = ProbeColCfg<NY>;
   const cudaError_t e = prep(k_probe_col<NY>, CC::SMEM);
   if (e != cudaSuccess) return e;
   k_probe_col<NY><<<batch_grid(ap.Wp / CC::C, P), CC::THREADS, CC::SMEM, st>>>(
@@ -977,8 +984,8 @@ cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, con
 template <int NX>
 static cudaError_t probe_row_n(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
                                cudaStream_t st) {
-  k_probe_row<NX><<<batch_grid(g.ny / RowCfg<NX>::G, P), RowCfg<NX>::THREADS, RowCfg<NX>::SMEM, st>>>(g, ap, Bpr, P,
-                                                                                                     scale, psi0);
+  using RC = ProbeRowCfg<NX>;
+  k_probe_row<NX><<<batch_grid(g.ny / RC::G, P), RC::THREADS, RC::SMEM, st>>>(g, ap, Bpr, P, scale, psi0);
   return cudaGetLastError();
 }
 cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, int P, float scale, float2* psi0,
@@ -991,8 +998,8 @@ static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane
                                const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
                                float2* Bpsi, cudaStream_t st) {
   const int nw = P * nfc;
-  const dim3 grid = batch_grid(g.ny / RowCfg<NX>::G, nw);
-  constexpr int TH = RowCfg<NX>::THREADS;
+  const dim3 grid = batch_grid(g.ny / SliceRowCfg<NX>::G, nw);
+  constexpr int TH = SliceRowCfg<NX>::THREADS;
 #define TACAW_SLICE_ROW(F, PL, TFU)                                                                               \
   do {                                                                                                            \
     constexpr int SM = SliceRowSmem<NX, TFU>::BYTES;                                                              \
@@ -1023,7 +1030,7 @@ static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const floa
                                const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
                                float2* Apsi, float2* psi_k, cudaStream_t st) {
   const int nw = P * nfc;
-  using CC = ColCfg<NY, Tuned<K_SLICE_COL, NY>::WIDE>;
+  using CC = SliceColCfg<NY>;
   const dim3 grid = batch_grid(b.Wp / CC::C, nw);
   constexpr int TH = CC::THREADS, SM = CC::SMEM;
   cudaError_t e = last ? prep(k_slice_col<NY, true>, SM) : prep(k_slice_col<NY, false>, SM);

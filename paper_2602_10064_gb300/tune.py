@@ -2,8 +2,9 @@
 
 Every FFT pass kernel (spreading row pass, potential and band-limit column passes, the row
 passes that form t, the multislice row and column passes) comes in variants: radix-16 or
-radix-8 plans (512 and 1024 points), two or three resident CTAs per SM, and for the column
-passes twice the columns per CTA.  No single choice is best for all of them: on GB300 the
+radix-8 plans (512 and 1024 points), 16 or 32 elements per thread (three- or two-pass
+transforms), two or three resident CTAs per SM, and for the column passes twice the columns
+per CTA.  No single choice is best for all of them: on GB300 the
 radix-8 plans speed up the 1024-point row passes, and three CTAs per SM speed up the
 spreading pass but slow down the multislice row pass.
 
@@ -14,7 +15,7 @@ replaces the default only when it is at least 2% faster.  Results of different v
 to FP32 rounding (the radix schedule changes the rounding order); the parity tests hold for
 every variant.
 
-    python -m paper_2602_10064_gb300.tune [--out PATH] [--variants 0 1 ... 7]
+    python -m paper_2602_10064_gb300.tune [--out PATH] [--variants 0 1 ... 14]
 
 Needs a GPU.  Synthetic inputs come from the repository's `workloads` module.
 """
@@ -134,7 +135,8 @@ def header(table: list, results: dict) -> str:
     lines = [
         "// Variant of each FFT pass kernel per transform length (see Tuned in k_slices.cu).",
         "// Written by paper_2602_10064_gb300/tune.py from CUDA-event timings of every variant on GB300",
-        "// (variant & 1: radix-8 plans; & 2: three CTAs per SM; & 4: wide column CTAs); ms per variant:",
+        "// (variant & 1: radix-8 plans; & 2: more resident threads; & 4: wide column CTAs; & 8: 32 elements",
+        "// per thread); ms per variant:",
     ]
     for key in sorted(set().union(*(r.keys() for r in results.values()))):
         lines.append("//   " + key + ": " + ", ".join(f"v{v} {r[key]:.2f}" for v, r in sorted(results.items())
@@ -156,7 +158,8 @@ def header(table: list, results: dict) -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(PKG, "csrc", "tuning_table.h"))
-    ap.add_argument("--variants", type=int, nargs="*", default=list(range(8)))
+    # bit 1 (radix-8 plans) has no effect together with bit 8 (32 elements per thread)
+    ap.add_argument("--variants", type=int, nargs="*", default=[v for v in range(16) if not (v & 8 and v & 1)])
     ap.add_argument("--measure", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.measure is not None:
