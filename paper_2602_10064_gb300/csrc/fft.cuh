@@ -299,28 +299,31 @@ struct GroupSync {
   }
 };
 
-// Shared-memory index of position x for one row-owned transform: one pad slot per 16
-// elements (per 8 for N <= 64).  With 64-bit accesses this keeps the own-position reads and
-// the stride-R writes of every pass at (or near) the minimum two wavefronts per warp.
-template <int N>
+// Shared-memory padding: one slot per 2^SH elements along the transform, 2^SH = E for 8, 16
+// and 32 elements per thread (16 for 12 and 24).  The first pass of every plan stores each
+// thread's E outputs contiguously (stride E across the threads of a warp); with one pad per E
+// those 64-bit stores, and the own-position reads of every pass, stay at (or near) the minimum
+// two wavefronts per warp.
+template <int N, int E>
 struct PadShift {
-  static constexpr int SH = N <= 64 ? 3 : 4;
+  static constexpr int SH = (E == 8 || N <= 64) ? 3 : (E == 32 ? 5 : 4);
 };
-template <int N>
+template <int N, int E>
 struct RowIdx {
-  static constexpr int SH = PadShift<N>::SH;
+  static constexpr int SH = PadShift<N, E>::SH;
   int base;
   __device__ __forceinline__ int operator()(int x) const { return base + x + (x >> SH); }
 };
-template <int N>
-__host__ __device__ constexpr int row_smem_stride() { return N + (N >> PadShift<N>::SH); }
+template <int N, int E>
+__host__ __device__ constexpr int row_smem_stride() { return N + (N >> PadShift<N, E>::SH); }
 
-// Column-owned transforms: C columns interleaved in shared memory, column c fastest (the
-// threads of one transform are spread over warps, so these transforms use BlockSync).
-template <int C>
+// Column-owned transforms: C columns interleaved in shared memory, column c fastest, padded
+// with one row of C slots per 2^SH rows (SH = 0: unpadded); the threads of one transform are
+// spread over warps, so these transforms use BlockSync.
+template <int C, int SH>
 struct ColIdx {
   int c;
-  __device__ __forceinline__ int operator()(int x) const { return x * C + c; }
+  __device__ __forceinline__ int operator()(int x) const { return (x + (SH ? (x >> SH) : 0)) * C + c; }
 };
 
 // One Stockham pass of radix R; NS = product of earlier radices.

@@ -76,7 +76,7 @@ struct RowCfg {
   static constexpr int G0 = (TARGET / 2) / T;
   static constexpr int G = G0 > 32 ? 32 : (G0 < 1 ? 1 : floor_pow2(G0));  // rows per CTA
   static constexpr int THREADS = G * T;
-  static constexpr int SMEM = G * row_smem_stride<N>() * (int)sizeof(float2);
+  static constexpr int SMEM = G * row_smem_stride<N, E>() * (int)sizeof(float2);
 };
 
 // Column passes: C columns per CTA (about 256 threads; WIDE doubles C, about 512 threads).
@@ -88,7 +88,9 @@ struct ColCfg {
   static constexpr int C0 = ((TARGET / 2) << WIDE) / T;
   static constexpr int C = C0 > 32 ? 32 : (C0 < 4 ? 4 : floor_pow2(C0));  // columns per CTA (divides Wp)
   static constexpr int THREADS = C * T;
-  static constexpr int SMEM = N * C * (int)sizeof(float2);
+  // padding of the interleaved columns: measured to pay only with 32 elements per thread
+  static constexpr int SH = E == 32 ? 5 : 0;
+  static constexpr int SMEM = (N + (SH ? (N >> SH) : 0)) * C * (int)sizeof(float2);
 };
 
 // The configuration of each pass kernel; a kernel and its launcher name the same alias.
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(SplatCfg<NX>::THREADS, minb_of<K_SPLAT_ROW, NX
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = acc[g * NX + t + T * e];
   __syncthreads();  // the FFT scratch of one group overlaps the accumulators of the next
-  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+  fft<NX, -1, PL>(v, sm, RowIdx<NX, E>{g * row_smem_stride<NX, E>()}, t, geo.tw + tw_offset(NX),
                   group_sync<T>(g));
   store_row_compact<NX>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
 }
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(ColPotCfg<NY>::THREADS, minb_of<K_COL_POT, NY,
   const int fs = batch_index();
   if (fs >= nbatch) return;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
-  const ColIdx<C> idx{c};
+  const ColIdx<C, CC::SH> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
   if constexpr (ONE) {
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(PotOutCfg<NX>::THREADS, minb_of<K_ROW_POT_OUT,
   const int fs = batch_index();
   if (fs >= nbatch) return;
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
-  const RowIdx<NX> idx{g * row_smem_stride<NX>()};
+  const RowIdx<NX, E> idx{g * row_smem_stride<NX, E>()};
   const auto sync = group_sync<T>(g);
   float2 v[E];
   load_row_compact<NX>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(RowVtCfg<NX>::THREADS, minb_of<K_ROW_VT, NX, R
     for (int e = 0; e < E; ++e) out[row + t + T * e] = v[e];
     return;
   }
-  fft<NX, -1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+  fft<NX, -1, PL>(v, sm, RowIdx<NX, E>{g * row_smem_stride<NX, E>()}, t, geo.tw + tw_offset(NX),
                   group_sync<T>(g));
   store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(ColTCfg<NY>::THREADS, minb_of<K_COL_T, NY, Col
   const int fs = batch_index();
   if (fs >= nbatch) return;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
-  const ColIdx<C> idx{c};
+  const ColIdx<C, CC::SH> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
   const float2* src = Bt + (size_t)fs * NY * b.Wp + cc;
@@ -653,7 +655,7 @@ __global__ void __launch_bounds__(RowToutCfg<NX>::THREADS, minb_of<K_ROW_TOUT, N
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, At + ((size_t)fs * ny + y) * b.Wp, b, t);
-  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+  fft<NX, +1, PL>(v, sm, RowIdx<NX, E>{g * row_smem_stride<NX, E>()}, t, geo.tw + tw_offset(NX),
                   group_sync<T>(g));
   float2* dst = tout + ((size_t)fs * ny + y) * NX;
 #pragma unroll
@@ -684,7 +686,7 @@ __global__ void __launch_bounds__(ProbeColCfg<NY>::THREADS, minb_of<K_PROBE_COL,
     v[e] = (abs(n) <= nb) ? amp * cmul(exv, ey[(size_t)p * NY + row]) : make_float2(0.f, 0.f);
     if (chi && abs(n) <= nb) v[e] = cmul(v[e], chi[(size_t)row * ap.Wp + cc]);
   }
-  fft<NY, +1, PL>(v, sm, ColIdx<C>{c}, t, geo.tw + tw_offset(NY), BlockSync{});
+  fft<NY, +1, PL>(v, sm, ColIdx<C, CC::SH>{c}, t, geo.tw + tw_offset(NY), BlockSync{});
   float2* dst = Bpr + (size_t)p * NY * ap.Wp + cc;
 #pragma unroll
   for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * ap.Wp] = v[e];
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(ProbeRowCfg<NX>::THREADS, minb_of<K_PROBE_ROW,
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   float2 v[E];
   load_row_compact<NX>(v, Bpr + ((size_t)p * ny + y) * ap.Wp, ap, t);
-  fft<NX, +1, PL>(v, sm, RowIdx<NX>{g * row_smem_stride<NX>()}, t, geo.tw + tw_offset(NX),
+  fft<NX, +1, PL>(v, sm, RowIdx<NX, E>{g * row_smem_stride<NX, E>()}, t, geo.tw + tw_offset(NX),
                   group_sync<T>(g));
   float2* dst = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW,
   if (w >= nwaves) return;
   const int g = threadIdx.x / T, t = threadIdx.x % T, y = blockIdx.x * G + g, ny = geo.ny;
   const int p = w / nfc, fl = w - p * nfc;
-  const RowIdx<NX> idx{g * row_smem_stride<NX>()};
+  const RowIdx<NX, E> idx{g * row_smem_stride<NX, E>()};
   const auto sync = group_sync<T>(g);
   float2 v[E];
   if (FIRST && PLANE && TF) {
@@ -786,7 +788,7 @@ __global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL,
   const int w = batch_index();
   if (w >= nwaves) return;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
-  const ColIdx<C> idx{c};
+  const ColIdx<C, CC::SH> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
   const float2* src = Bpsi + (size_t)w * NY * b.Wp + cc;
