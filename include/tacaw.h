@@ -268,6 +268,13 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
  * those calls are invalid), else TACAW_OK.  The status is cleared by the check. */
 int tacaw_check(tacaw_ctx* ctx);
 
+/* Self-test of the failure path of the bounded waits (the paper has no counterpart): one
+ * kernel thread waits on a shared-memory barrier that nothing completes, gives up after
+ * timeout_ms (0 < timeout_ms <= 1000) through the same bounded-wait routine the tensor-core
+ * time transform uses, sets the status word and returns; the next tacaw_check then reports
+ * TACAW_ETIMEOUT and the context stays usable.  No copy or MMA is in flight during the wait. */
+int tacaw_selftest_wait(tacaw_ctx* ctx, double timeout_ms, void* stream);
+
 /* Diagnostics.  tacaw_profile_begin starts recording a CUDA event pair around every kernel
  * launch of the calls that follow, on the stream each launch uses.  tacaw_profile_end stops,
  * waits for the recorded events and reports per kernel class i < max_n (in first-launch order):

@@ -128,6 +128,7 @@ def lib():
             "tacaw_spectrum": (C.c_int, [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp, vp]),
             "tacaw_run": (C.c_int, [vp, pp, vp, vp, i64, i64, prp, i32, i32, vp, vp]),
             "tacaw_check": (C.c_int, [vp]),
+            "tacaw_selftest_wait": (C.c_int, [vp, C.c_double, vp]),
             "tacaw_set_option": (C.c_int, [vp, C.c_char_p, i64]),
             "tacaw_spectral_diffraction": (C.c_int, [vp, vp, i64, i64, i64, C.c_double, C.c_double, i32, vp, vp]),
             "tacaw_dispersion": (C.c_int, [vp, vp, i64, i64, i32, i32, C.c_double, C.c_double, vp, vp, i32, vp,
@@ -156,7 +157,7 @@ def exported_symbols():
             "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end",
             "tacaw_spectrum_static", "tacaw_submit", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
             "tacaw_serving_stats", "tacaw_set_option", "tacaw_spectral_diffraction", "tacaw_dispersion",
-            "tacaw_accumulate"]
+            "tacaw_accumulate", "tacaw_selftest_wait"]
 
 
 def _ptr(x):
@@ -304,6 +305,11 @@ def tacaw_accumulate(ctx, S, n, weight, acc, stream=None):
 
 def tacaw_check(ctx):
     return _check(ctx, lib().tacaw_check(ctx))
+
+
+def tacaw_selftest_wait(ctx, timeout_ms, stream=None):
+    """Run one bounded wait that nothing completes (see the header); the next check reports it."""
+    return _check(ctx, lib().tacaw_selftest_wait(ctx, float(timeout_ms), _stream(stream)))
 
 
 def tacaw_profile_begin(ctx):

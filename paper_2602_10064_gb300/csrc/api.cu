@@ -499,6 +499,7 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
   CK(sc.get(&recs, (size_t)nf * std::max<int64_t>(A, 1)));
   CK(sc.get(&offs, (size_t)nf * (S + 1)));
   {
+    NvtxRange r_bin("binning");
     ProfScope ps(ctx, "bin", sc.st, (double)nf * A * 28, 0);
     CK(launch_bin(pos, A, nf, S, p.cell[0], p.cell[1], p.cell[2], p.nx, p.ny, slots, recs, offs, nullptr, sc.st));
   }
@@ -508,6 +509,7 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
   CK(sc.get(&rrecs, (size_t)nf * std::max<int64_t>(A, 1)));
   CK(sc.get(&boffs, (size_t)nf * S * (nyb + 1)));
   {
+    NvtxRange r_sort("binning_rows");
     ProfScope ps(ctx, "sort_rows", sc.st, (double)nf * A * 48 + (double)nf * S * (nyb + 1) * 4, 0);
     CK(launch_sort_rows(recs, offs, A, nf, S, ny, rrecs, boffs, sc.st));
   }
@@ -523,15 +525,18 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
     for (int s0 = 0; s0 < S; s0 += sb) {
       const int sbc = std::min(sb, S - s0), nfs = nfc * sbc;
       {
-        ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
-                     (double)nfs * g->npair * ny * fx);
-        CK(launch_splat_row(geo, g->band, rrecs + (size_t)f0 * A, boffs + (size_t)f0 * S * (nyb + 1), A, S, s0,
-                            sbc, nfs, g->npair, sk, Bp, sc.st));
-      }
-      {
-        ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
-                     (double)nfs * (g->npair + 1) * g->band.W * fy);
-        CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
+        NvtxRange r_pot("potential");
+        {
+          ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
+                       (double)nfs * g->npair * ny * fx);
+          CK(launch_splat_row(geo, g->band, rrecs + (size_t)f0 * A, boffs + (size_t)f0 * S * (nyb + 1), A, S, s0,
+                              sbc, nfs, g->npair, sk, Bp, sc.st));
+        }
+        {
+          ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
+                       (double)nfs * (g->npair + 1) * g->band.W * fy);
+          CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
+        }
       }
       TRY_RC(sink(f0, nfc, s0, sbc, Ap));
     }
@@ -798,9 +803,14 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
   TRY_RC(trans_bufs(ctx, p, g, rt.chunk * rt.sb, tf, sc, &tb));
   TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, rt.chunk, rt.sb, sc,
                           [&](int64_t f0, int nfc, int s0, int sbc, float2* Ap) {
-    TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * sbc, t, sc, tb, tf));
+    {
+      NvtxRange r("transmission");
+      TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * sbc, t, sc, tb, tf));
+    }
+    NvtxRange r("multislice");
     return slices(ctx, p, g, t, nfc, s0, sbc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
   }));
+  NvtxRange r("time_dft");
   return spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc);
 }
 
@@ -812,6 +822,7 @@ int tacaw_bin_slices(tacaw_ctx* ctx, const tacaw_params* params, const float* po
                      int32_t* slice_out, void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw::NvtxRange nvtx("tacaw_bin_slices");
   TRY_RC(check_params(ctx, params));
   if (n_atoms < 0 || nf < 1) return set_err(ctx, TACAW_EINVAL, "n_atoms >= 0 and nf >= 1 required");
   if (n_atoms == 0) return TACAW_OK;
@@ -830,6 +841,7 @@ int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const floa
                           int64_t n_atoms, int64_t nf, float* V_out, void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw::NvtxRange nvtx("tacaw_build_potential");
   TRY_RC(check_params(ctx, params));
   const tacaw_params& p = *params;
   if (n_atoms < 0 || nf < 1) return set_err(ctx, TACAW_EINVAL, "n_atoms >= 0 and nf >= 1 required");
@@ -859,6 +871,7 @@ int tacaw_transmission(tacaw_ctx* ctx, const tacaw_params* params, const float* 
                        void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw::NvtxRange nvtx("tacaw_transmission");
   TRY_RC(check_params(ctx, params));
   if (nf < 1) return set_err(ctx, TACAW_EINVAL, "nf >= 1 required");
   if (!is_device_ptr(V) || !is_device_ptr(t_out)) return set_err(ctx, TACAW_EINVAL, "V, t_out must be device pointers");
@@ -882,6 +895,7 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
                     float* psi_k_out, void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw::NvtxRange nvtx("tacaw_propagate");
   TRY_RC(check_params(ctx, params));
   const tacaw_params& p = *params;
   tacaw_probe pr = probe ? *probe : default_probe();
@@ -923,6 +937,7 @@ int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int
                    int32_t reduce, const int32_t* q_sel, int64_t n_sel, float* S_out, void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw::NvtxRange nvtx("tacaw_spectrum");
   if (P < 1 || F < 1 || nq < 1) return set_err(ctx, TACAW_EINVAL, "P, F, nq must be >= 1");
   if (!is_device_ptr(psi_k) || !is_device_ptr(S_out) || (q_sel && !is_device_ptr(q_sel)))
     return set_err(ctx, TACAW_EINVAL, "psi_k, S_out (and q_sel) must be device pointers");
@@ -938,6 +953,7 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
               void* stream) {
   if (!ctx) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw::NvtxRange nvtx("tacaw_run");
   tacaw_probe pr = probe ? *probe : default_probe();
   TRY_RC(check_run(ctx, params, pr, pos, Z, n_atoms, n_frames, precision, reduce, S_out));
   const tacaw_params& p = *params;

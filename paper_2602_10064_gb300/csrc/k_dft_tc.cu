@@ -73,11 +73,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: false (and the status word set) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status,
+                                          unsigned long long timeout_ns = TC_TIMEOUT_NS) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (!mbar_try(bar, parity)) {
-    if (globaltimer() - t0 > TC_TIMEOUT_NS) {
+    if (globaltimer() - t0 > timeout_ns) {
       atomicOr(status, TC_ERR_TIMEOUT);
       return false;
     }
@@ -366,6 +367,18 @@ __global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict
   }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing ever arrives on,
+// with a short limit, so the wait runs out, sets the status word and returns (no copy or MMA
+// is in flight, no TMEM is held).
+__global__ void k_wait_selftest(int* __restrict__ status, unsigned long long timeout_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait(b, 0, status, timeout_ns);
+}
+
 // ---------------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------------
@@ -535,3 +548,16 @@ int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_
 }
 
 }  // namespace tacaw
+
+extern "C" int tacaw_selftest_wait(tacaw_ctx* ctx, double timeout_ms, void* stream) {
+  using namespace tacaw;
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (!(timeout_ms > 0.0) || timeout_ms > 1000.0) return set_err(ctx, TACAW_EINVAL, "timeout_ms must be in (0, 1000]");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(ctx->d_status, (unsigned long long)(timeout_ms * 1e6));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "k_wait_selftest");
+  return TACAW_OK;
+}

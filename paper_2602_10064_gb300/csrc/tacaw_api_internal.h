@@ -2,6 +2,7 @@
 // caches, stream-ordered scratch and the error helpers.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <memory>
@@ -14,6 +15,17 @@
 
 namespace tacaw {
 struct Serving;
+
+// NVTX range over a scope of host code (an entry point or a phase of a run).  The calls only
+// enqueue work, so a range marks the host-side issue of its launches; profilers that filter by
+// range (ncu --nvtx --nvtx-include "tacaw_run/") select the kernels launched inside it.  Without
+// an attached tool the push and pop do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 }
 
 struct GeoCache {

@@ -164,6 +164,25 @@ def test_run_unknown_species_on_device_reported_by_check(ctx, T):
     assert rel(good, oracle.tacaw(w)) < TOL_S
 
 
+def test_bounded_wait_runs_out_and_is_reported(ctx, T):
+    """The failure path of the kernels' bounded waits, without a GPU fault: a wait on a barrier
+    that nothing completes gives up after 20 ms, tacaw_check reports ETIMEOUT once, and the
+    context keeps working."""
+    ctx.check()
+    T.tacaw_selftest_wait(ctx.h, 20.0)
+    with pytest.raises(T.TacawError) as ei:
+        ctx.check()
+    assert ei.value.code == T.TACAW_ETIMEOUT
+    ctx.check()  # cleared
+    w = workloads.diamond_si(n_frames=4, grid=32, n_slices=2, reps=(1, 1, 1))
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
+    ctx.check()
+    assert rel(S, oracle.tacaw(w)) < TOL_S
+    with pytest.raises(T.TacawError):
+        T.tacaw_selftest_wait(ctx.h, 0.0)
+
+
 def test_run_does_not_block_the_host(ctx, T):
     """With every buffer on the device, tacaw_run only enqueues work: the call returns while
     an earlier long run is still executing on the same stream."""
@@ -537,7 +556,7 @@ def test_spectrum_single_product_is_coarser(ctx, T):
 def test_run_config1_tensor_core(ctx, T):
     w = workloads.config1()
     ctx.load_form_factors(w.form_Z, w.form_coef)
-    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w), precision=T.DFT_BF16X3).cpu().numpy()
+    S = ctx.run(T.params_of(w), dev(w.pos), dev(w.Z), T.probe_of(w)).cpu().numpy()
     ctx.check()
     ref = oracle.tacaw(w)
     err = rel(S, ref)
