@@ -395,6 +395,21 @@ def test_time_roll_and_reversal():
     assert rel(S_rev, S[:, neg]) < 1e-12
 
 
+def test_periodic_trajectory_spectrum():
+    """A trajectory that repeats every R frames: S over F = k R frames is k^2 times the R-frame
+    spectrum at omega = m k and zero elsewhere (the DFT of a periodic sequence).  The full-size
+    GPU tests build their reference this way."""
+    w = workloads.diamond_si(n_frames=4, grid=32, n_slices=4, seed=12)
+    p = oracle.params_of(w)
+    psi = oracle.multislice(p, w.pos, w.Z, w.form_Z, w.form_coef)
+    R, k = 4, 6
+    S_R = oracle.spectrum(psi)
+    S_F = oracle.spectrum(np.tile(psi, (1, k, 1, 1)))
+    assert rel(S_F[:, ::k], k * k * S_R) < 1e-12
+    off = np.delete(S_F, np.arange(0, R * k, k), axis=1)
+    assert np.abs(off).max() < 1e-12 * S_F.max()
+
+
 def test_lattice_translation_invariance():
     w = workloads.diamond_si(n_frames=8, grid=32, n_slices=4, seed=12)
     p = oracle.params_of(w)
