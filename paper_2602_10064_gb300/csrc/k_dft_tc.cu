@@ -1,8 +1,8 @@
 // Tensor-core time transform (Methods, "Workflow Architecture": psi~(k, w) = F_t[psi - <psi>_t],
 // I = |psi~|^2) as a dense real GEMM on the 5th-generation tensor cores (tcgen05).
 //
-// With W = exp(-2 pi i w n / F) = cos - i sin and the residual r_n = psi_n - <psi> (FP64), the
-// complex sum becomes the real product D = A B^T:
+// With W = exp(-2 pi i w n / F) = cos - i sin and the residual r_n = psi_n - <psi> (formed exactly
+// from the FP64-class mean), the complex sum becomes the real product D = A B^T:
 //   rows of D: m = 2w + c (c = 0 real, 1 imaginary part of psi~(w)),
 //   K:         kappa = 2n + c' (c' = 0 real, 1 imaginary part of r_n),
 //   A[2w][2n] = cos, A[2w][2n+1] = sin, A[2w+1][2n] = -sin, A[2w+1][2n+1] = cos,
@@ -304,8 +304,10 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Residual split: B_hi/B_lo[J][2n + c] for J = p * nsel + j, from r = psi[p][n][q_j] - mean[p][j]
-// (FP64), zero for K pad columns.  32 x 32 (j, n) tile per CTA, transposed through shared memory.
+// Residual split: B_hi/B_lo[J][2n + c] for J = p * nsel + j, from r = psi[p][n][q_j] - mean[p][j],
+// zero for K pad columns.  32 x 32 (j, n) tile per CTA, transposed through shared memory.  The
+// difference is formed exactly as the FP32 pair (r, re) (pair_sub: the FP64 mean as an FP32
+// pair); hi = r rounded to the operand type, lo = (r - hi) + re, where r - hi is exact.
 template <bool TF32>
 __global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict__ psi, const double2* __restrict__ mean,
                                                         int64_t F, int64_t nq, const int32_t* __restrict__ qsel,
@@ -319,27 +321,30 @@ __global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict
   // phase 1: coalesced along j
   const int64_t J = J0 + tx;
   int64_t p = 0, j = 0, q = 0;
-  double2 mu = make_double2(0.0, 0.0);
+  float mxh = 0.f, mxl = 0.f, myh = 0.f, myl = 0.f;
   if (J < ncols) {
     p = J / nsel;
     j = J - p * nsel;
     q = qsel ? qsel[j] : j;
-    mu = mean[(size_t)p * nsel + j];
+    const double2 mu = mean[(size_t)p * nsel + j];
+    split_double(mu.x, mxh, mxl);
+    split_double(mu.y, myh, myl);
   }
   for (int r = ty; r < 32; r += 8) {
     const int64_t n = n0 + r;
     float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
     if (J < ncols && n < F) {
       const float2 v = psi[((size_t)p * F + n) * nq + q];
-      const double re = (double)v.x - mu.x, im = (double)v.y - mu.y;
+      float rx, ex, ry, ey;
+      pair_sub(v.x, mxh, mxl, rx, ex);
+      pair_sub(v.y, myh, myl, ry, ey);
       if (TF32) {
-        const float ah = to_tf32((float)re), bh = to_tf32((float)im);
+        const float ah = to_tf32(rx), bh = to_tf32(ry);
         h = make_float2(ah, bh);
-        l = make_float2(to_tf32((float)(re - (double)ah)), to_tf32((float)(im - (double)bh)));
+        l = make_float2(to_tf32(__fadd_rn(__fsub_rn(rx, ah), ex)), to_tf32(__fadd_rn(__fsub_rn(ry, bh), ey)));
       } else {
-        const __nv_bfloat16 ah = __float2bfloat16_rn((float)re), bh = __float2bfloat16_rn((float)im);
-        h = make_float2(__bfloat162float(ah), __bfloat162float(bh));
-        l = make_float2((float)(re - (double)h.x), (float)(im - (double)h.y));
+        h = make_float2(__bfloat162float(__float2bfloat16_rn(rx)), __bfloat162float(__float2bfloat16_rn(ry)));
+        l = make_float2(__fadd_rn(__fsub_rn(rx, h.x), ex), __fadd_rn(__fsub_rn(ry, h.y), ey));
       }
     }
     hs[r][tx] = h;

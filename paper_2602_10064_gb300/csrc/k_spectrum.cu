@@ -1,7 +1,7 @@
 // Time transform (Methods, "Workflow Architecture"):
 //   psi~(k, w) = F_t[psi(k, t) - <psi(k, t)>_t],  I(k, w) = |psi~(k, w)|^2.
-// The mean over frames and the residual are formed in FP64 (the elastic part is large and the
-// inelastic signal is a small difference).  This file holds the plain FP32 SIMT dense DFT;
+// The mean over frames and the residual are formed to FP64-class precision (the elastic part
+// is large and the inelastic signal is a small difference), as FP32 pairs.  This file holds the plain FP32 SIMT dense DFT;
 // the tensor-core variants are in k_dft_tc.cu.
 #include <cuda_runtime.h>
 
@@ -9,31 +9,65 @@
 
 namespace tacaw {
 
-// mean[p][j] = (1/F) sum_n psi[p][n][q_j], FP64.
-__global__ void k_mean_f64(const float2* __restrict__ psi, int64_t F, int64_t nq, const int32_t* __restrict__ qsel,
-                           int64_t nsel, double2* __restrict__ mean) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// mean[p][j] = (1/F) sum_n psi[p][n][q_j] to FP64-class precision.  A CTA takes 32 columns;
+// 8 threads per column sum the frames n = g mod 8 (four loads in flight each) as FP32 pairs
+// (pair_add), in frame order; the 8 pairs are then added in FP64 in a fixed order and divided
+// by F.  Over n frames a pair loses at most about n 2^-48 of its largest partial sum (FP64
+// summation: n 2^-53), far below the FP32 rounding of the residual that follows.
+constexpr int MEAN_COLS = 32, MEAN_GROUPS = 8;
+
+__global__ void __launch_bounds__(MEAN_COLS * MEAN_GROUPS)
+    k_mean_f64(const float2* __restrict__ psi, int64_t F, int64_t nq, const int32_t* __restrict__ qsel,
+               int64_t nsel, double2* __restrict__ mean) {
+  __shared__ float4 part[MEAN_GROUPS][MEAN_COLS];  // (hi.x, lo.x, hi.y, lo.y)
+  const int tx = threadIdx.x % MEAN_COLS, g = threadIdx.x / MEAN_COLS;
+  const int64_t j = blockIdx.x * (int64_t)MEAN_COLS + tx;
   const int64_t p = blockIdx.y;
-  if (j >= nsel) return;
-  const int64_t q = qsel ? qsel[j] : j;
-  const float2* col = psi + (size_t)p * F * nq + q;
-  double sr = 0.0, si = 0.0;
-  for (int64_t n = 0; n < F; ++n) {
-    const float2 v = col[(size_t)n * nq];
-    sr += (double)v.x;
-    si += (double)v.y;
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+  if (j < nsel) {
+    const int64_t q = qsel ? qsel[j] : j;
+    const float2* col = psi + (size_t)p * F * nq + q;
+    int64_t n = g;
+    for (; n + 3 * MEAN_GROUPS < F; n += 4 * MEAN_GROUPS) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = col[(size_t)(n + u * MEAN_GROUPS) * nq];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        pair_add(hx, lx, v[u].x);
+        pair_add(hy, ly, v[u].y);
+      }
+    }
+    for (; n < F; n += MEAN_GROUPS) {
+      const float2 v = col[(size_t)n * nq];
+      pair_add(hx, lx, v.x);
+      pair_add(hy, ly, v.y);
+    }
   }
-  mean[(size_t)p * nsel + j] = make_double2(sr / (double)F, si / (double)F);
+  part[g][tx] = make_float4(hx, lx, hy, ly);
+  __syncthreads();
+  if (g == 0 && j < nsel) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int k = 0; k < MEAN_GROUPS; ++k) {
+      const float4 a = part[k][tx];
+      sx += (double)a.x + (double)a.y;
+      sy += (double)a.z + (double)a.w;
+    }
+    mean[(size_t)p * nsel + j] = make_double2(sx / (double)F, sy / (double)F);
+  }
 }
 
 cudaError_t launch_mean_f64(const float2* psi, int64_t P, int64_t F, int64_t nq, const int32_t* qsel, int64_t nsel,
                             double2* mean, cudaStream_t st) {
   if (P > 65535) return cudaErrorInvalidValue;
-  k_mean_f64<<<dim3((unsigned)((nsel + 255) / 256), (unsigned)P), 256, 0, st>>>(psi, F, nq, qsel, nsel, mean);
+  k_mean_f64<<<dim3((unsigned)((nsel + MEAN_COLS - 1) / MEAN_COLS), (unsigned)P), MEAN_COLS * MEAN_GROUPS, 0, st>>>(
+      psi, F, nq, qsel, nsel, mean);
   return cudaGetLastError();
 }
 
-// r[p][n][j] = psi[p][n][q_j] - mean[p][j], subtraction in FP64, rounded to float.
+// r[p][n][j] = psi[p][n][q_j] - mean[p][j]: the mean as an FP32 pair, the difference formed
+// exactly (pair_sub) and rounded to float.
 __global__ void k_residual_f32(const float2* __restrict__ psi, const double2* __restrict__ mean, int64_t F,
                                int64_t nq, const int32_t* __restrict__ qsel, int64_t nsel, float2* __restrict__ r) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -42,7 +76,12 @@ __global__ void k_residual_f32(const float2* __restrict__ psi, const double2* __
   const int64_t q = qsel ? qsel[j] : j;
   const float2 v = psi[((size_t)p * F + n) * nq + q];
   const double2 m = mean[(size_t)p * nsel + j];
-  r[((size_t)p * F + n) * nsel + j] = make_float2((float)((double)v.x - m.x), (float)((double)v.y - m.y));
+  float mxh, mxl, myh, myl, rx, ex, ry, ey;
+  split_double(m.x, mxh, mxl);
+  split_double(m.y, myh, myl);
+  pair_sub(v.x, mxh, mxl, rx, ex);
+  pair_sub(v.y, myh, myl, ry, ey);
+  r[((size_t)p * F + n) * nsel + j] = make_float2(rx, ry);
 }
 
 cudaError_t launch_residual_f32(const float2* psi, const double2* mean, int64_t P, int64_t F, int64_t nq,

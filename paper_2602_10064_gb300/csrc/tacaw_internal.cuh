@@ -47,6 +47,35 @@ struct AtomRec {
 };
 
 __device__ __forceinline__ int fftfreq_index(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+
+// Error-free FP32 sums (Knuth's two-sum): s = fl(a + b) and e with s + e = a + b exactly.
+// GB300's FP64 pipe issues at 1/64 of the FP32 rate, so the elastic mean and the residual
+// carry FP64-class precision as unevaluated FP32 pairs built from these, not as doubles.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// Running sum as the pair (hi, lo), |lo| <= 2^-24 |hi|: hi takes x by a two-sum, lo takes the
+// exact error, then the pair is renormalised by a second two-sum (exact whichever part is
+// larger).  Each step loses at most about 2^-48 |hi|.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  two_sum(s, __fadd_rn(lo, e), hi, lo);
+}
+// The FP64 value m as an FP32 pair: hi = fl32(m), lo = fl32(m - hi) (m - hi is exact in FP64).
+__device__ __forceinline__ void split_double(double m, float& hi, float& lo) {
+  hi = (float)m;
+  lo = (float)(m - (double)hi);
+}
+// x - (mh + ml) as the pair (r, re): r = fl32 of the difference, r + re the difference to
+// within |ml| * 2^-24 + 2^-48 |x - mh| (x - mh is formed exactly).
+__device__ __forceinline__ void pair_sub(float x, float mh, float ml, float& r, float& re) {
+  float s, e;
+  two_sum(x, -mh, s, e);
+  two_sum(s, __fsub_rn(e, ml), r, re);
+}
 __device__ __forceinline__ int band_col_x(const Band& b, int nx, int c) { return c <= b.mb ? c : nx - (b.W - c); }
 __device__ __forceinline__ int band_x_col(const Band& b, int nx, int x) {
   return x <= b.mb ? x : (x >= nx - b.mb ? x - nx + b.W : -1);
@@ -113,7 +142,9 @@ cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot,
 // ---- time transform (k_spectrum.cu) -----------------------------------------------------
 cudaError_t launch_mean_f64(const float2* psi, int64_t P, int64_t F, int64_t nq, const int32_t* qsel,
                             int64_t nsel, double2* mean, cudaStream_t st);
-// residual r[p][n][j] = psi[p][n][qsel[j]] - mean[p][j] in FP64, rounded to float
+// mean[p][j] = (1/F) sum_n psi[p][n][qsel[j]]: FP32 pair sums, combined and divided in FP64
+// residual r[p][n][j] = psi[p][n][qsel[j]] - mean[p][j], formed exactly as an FP32 pair and
+// rounded to float
 cudaError_t launch_residual_f32(const float2* psi, const double2* mean, int64_t P, int64_t F, int64_t nq,
                                 const int32_t* qsel, int64_t nsel, float2* r, cudaStream_t st);
 // S[p][m][qsel[j]] = |sum_n W[m][n] r[p][n][j]|^2 (FP32), W from the length-F table

@@ -357,6 +357,19 @@ def test_spectrum_mean_subtraction_fp64(ctx, T):
     assert rel(S, ref) < 1e-5
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 2e-5), ("tf32x3", 2e-5)])
+def test_spectrum_elastic_ratio_1e7_over_1024_frames(ctx, T, prec, tol):
+    """An elastic part 1e7 times the fluctuation, summed over 1024 frames: an FP32 running sum
+    of the mean would be off by about 7e-6 of the elastic part, 80 times the signal.  The
+    FP32-pair sums and the exact differences hold every precision to its FP32-input tolerance."""
+    psi = workloads.random_exit_waves(2, 1024, 300, seed=19, elastic=1e4, inelastic=1e-3)
+    code = {"fp32": T.DFT_FP32, "bf16x3": T.DFT_BF16X3, "tf32x3": T.DFT_TF32X3}[prec]
+    S = ctx.spectrum(dev(psi), precision=code).cpu().numpy()
+    ctx.check()
+    ref = oracle.spectrum(psi)
+    assert rel(S, ref) < tol, rel(S, ref)
+
+
 # ------------------------------------------------------------------------------------------
 # the whole path
 # ------------------------------------------------------------------------------------------
