@@ -284,6 +284,13 @@ int tacaw_selftest_wait(tacaw_ctx* ctx, double timeout_ms, void* stream);
 int tacaw_profile_begin(tacaw_ctx* ctx);
 int tacaw_profile_end(tacaw_ctx* ctx, char* names, double* ms, int64_t* launches, double* bytes, double* flops,
                       int32_t max_n, int32_t* n_out);
+/* Restricts the event pairs of the profiles that follow to the kernel classes named in `names`
+ * (comma-separated, e.g. "slice_row,slice_col"; NULL or "" selects every class).  Launches of
+ * the other classes are still counted, with their algorithmic bytes and flops, but get no events
+ * and report 0 milliseconds, so the profile adds almost nothing to the time of unselected
+ * launches.  The selection stays until the next call.  TACAW_EINVAL while a profile is being
+ * recorded.  The paper has no counterpart. */
+int tacaw_profile_select(tacaw_ctx* ctx, const char* names);
 
 #ifdef __cplusplus
 }

@@ -142,6 +142,7 @@ def lib():
             "tacaw_serving_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_uint64),
                                               C.POINTER(C.c_uint64)]),
             "tacaw_profile_begin": (C.c_int, [vp]),
+            "tacaw_profile_select": (C.c_int, [vp, C.c_char_p]),
             "tacaw_profile_end": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)]),
         }
         for name, (res, args) in sig.items():
@@ -154,7 +155,7 @@ def lib():
 def exported_symbols():
     return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
-            "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_end",
+            "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_select", "tacaw_profile_end",
             "tacaw_spectrum_static", "tacaw_submit", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
             "tacaw_serving_stats", "tacaw_set_option", "tacaw_spectral_diffraction", "tacaw_dispersion",
             "tacaw_accumulate", "tacaw_selftest_wait"]
@@ -314,6 +315,12 @@ def tacaw_selftest_wait(ctx, timeout_ms, stream=None):
 
 def tacaw_profile_begin(ctx):
     return _check(ctx, lib().tacaw_profile_begin(ctx))
+
+
+def tacaw_profile_select(ctx, names=""):
+    """Time only the named kernel classes (comma-separated) in the profiles that follow; the
+    other launches are counted with 0 ms.  "" times every class."""
+    return _check(ctx, lib().tacaw_profile_select(ctx, (names or "").encode()))
 
 
 def tacaw_profile_end(ctx, max_n=64):

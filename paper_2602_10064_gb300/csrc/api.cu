@@ -136,6 +136,11 @@ ProfScope::ProfScope(tacaw_ctx* c, const char* name, cudaStream_t s, double byte
   rec.name = name;
   rec.bytes = bytes;
   rec.flops = flops;
+  const auto& sel = c->prof.select;
+  if (!sel.empty() && std::find(sel.begin(), sel.end(), name) == sel.end()) {
+    c->prof.recs.push_back(rec);  // counted, not timed (no events)
+    return;
+  }
   rec.a = prof_event(c);
   rec.b = prof_event(c);
   if (!rec.a || !rec.b) return;
@@ -458,6 +463,7 @@ int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, bo
                int8_t** d_slot) {
   if (z_on_device && device_check) {
     CK(sc.get(d_slot, std::max<int64_t>(A, 1)));
+    ProfScope ps(ctx, "map_slots", sc.st, (double)A * 5, 0);
     CK(launch_map_slots(Z, A, ctx->d_zslot, *d_slot, ctx->d_status, sc.st));
     return TACAW_OK;
   }
@@ -665,8 +671,14 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
   CK(cudaMemcpyAsync(d_ey, ey.data(), sizeof(float2) * ey.size(), cudaMemcpyHostToDevice, sc.st));
   const Band ap{W, Wp, mb, d_nb};
   const Geo geo{nx, ny, ctx->tw};
-  CK(launch_probe_col(geo, ap, d_ex, d_ey, d_chi, P, (float)(1.0 / std::sqrt((double)count)), Bpr, sc.st));
-  CK(launch_probe_row(geo, ap, Bpr, P, (float)(1.0 / std::sqrt((double)nx * ny)), *psi0, sc.st));
+  {
+    ProfScope ps(ctx, "probe_col", sc.st, (double)P * ny * Wp * 8, (double)P * W * 5.0 * ny * std::log2((double)ny));
+    CK(launch_probe_col(geo, ap, d_ex, d_ey, d_chi, P, (float)(1.0 / std::sqrt((double)count)), Bpr, sc.st));
+  }
+  {
+    ProfScope ps(ctx, "probe_row", sc.st, (double)P * ny * (Wp + nx) * 8, (double)P * ny * 5.0 * nx * std::log2((double)nx));
+    CK(launch_probe_row(geo, ap, Bpr, P, (float)(1.0 / std::sqrt((double)nx * ny)), *psi0, sc.st));
+  }
   return TACAW_OK;
 }
 
@@ -1032,6 +1044,24 @@ int tacaw_profile_begin(tacaw_ctx* ctx) {
   return TACAW_OK;
 }
 
+int tacaw_profile_select(tacaw_ctx* ctx, const char* names) {
+  if (!ctx) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  if (ctx->prof.on) return set_err(ctx, TACAW_EINVAL, "tacaw_profile_select while a profile is being recorded");
+  ctx->prof.select.clear();
+  if (!names) return TACAW_OK;
+  std::string cur;
+  for (const char* c = names;; ++c) {
+    if (*c == ',' || *c == 0) {
+      if (!cur.empty()) ctx->prof.select.push_back(cur);
+      cur.clear();
+      if (*c == 0) break;
+    } else if (*c != ' ') {
+      cur.push_back(*c);
+    }
+  }
+  return TACAW_OK;
+}
 int tacaw_profile_end(tacaw_ctx* ctx, char* names, double* ms, int64_t* launches, double* bytes, double* flops,
                       int32_t max_n, int32_t* n_out) {
   if (!ctx) return TACAW_EINVAL;
@@ -1040,9 +1070,11 @@ int tacaw_profile_end(tacaw_ctx* ctx, char* names, double* ms, int64_t* launches
   std::vector<std::string> order;
   std::map<std::string, std::tuple<double, int64_t, double, double>> acc;
   for (const ProfRec& r : ctx->prof.recs) {
-    CK(cudaEventSynchronize(r.b));
     float t = 0.f;
-    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    if (r.a) {
+      CK(cudaEventSynchronize(r.b));
+      CK(cudaEventElapsedTime(&t, r.a, r.b));
+    }
     if (!acc.count(r.name)) order.push_back(r.name);
     auto& a = acc[r.name];
     std::get<0>(a) += t;

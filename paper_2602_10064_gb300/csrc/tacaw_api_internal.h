@@ -55,6 +55,7 @@ struct Profiler {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   size_t next = 0;
+  std::vector<std::string> select;  // classes timed with events; empty: every class
 };
 
 struct tacaw_ctx {

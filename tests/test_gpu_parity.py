@@ -183,6 +183,32 @@ def test_bounded_wait_runs_out_and_is_reported(ctx, T):
         T.tacaw_selftest_wait(ctx.h, 0.0)
 
 
+def test_profile_select_times_only_the_named_class(ctx, T):
+    """With a selection, only the named kernel class gets event pairs; every launch of the
+    other classes is still counted, with 0 ms."""
+    w = workloads.diamond_si(n_frames=4, grid=32, n_slices=2, reps=(1, 1, 1))
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p, pr = T.params_of(w), T.probe_of(w)
+    pos, Z = dev(w.pos), dev(w.Z)
+    T.tacaw_profile_begin(ctx.h)
+    ctx.run(p, pos, Z, pr)
+    full = T.tacaw_profile_end(ctx.h)
+    T.tacaw_profile_select(ctx.h, "slice_row")
+    try:
+        T.tacaw_profile_begin(ctx.h)
+        with pytest.raises(T.TacawError):
+            T.tacaw_profile_select(ctx.h, "")  # not while a profile is being recorded
+        ctx.run(p, pos, Z, pr)
+        sel = T.tacaw_profile_end(ctx.h)
+    finally:
+        T.tacaw_profile_select(ctx.h, "")
+    ctx.check()
+    assert "slice_row" in full and "map_slots" in full
+    assert {k: v[1] for k, v in sel.items()} == {k: v[1] for k, v in full.items()}
+    assert sel["slice_row"][0] > 0.0
+    assert all(v[0] == 0.0 for k, v in sel.items() if k != "slice_row")
+
+
 def test_run_does_not_block_the_host(ctx, T):
     """With every buffer on the device, tacaw_run only enqueues work: the call returns while
     an earlier long run is still executing on the same stream."""
