@@ -142,7 +142,8 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
 
 /* Time transform (Methods, "Workflow Architecture"): for every (p, q)
  * S[p][m][q] = |sum_n (psi[p][n][q] - mean_n psi[p][n][q]) exp(-2 pi i m n / F)|^2,
- * the mean and the residual in FP64, the sum by the arithmetic `precision` (TACAW_DFT_*).
+ * the mean and the residual to FP64-class precision (FP32-pair sums and exact differences,
+ * combined in FP64 once per q), the sum by the arithmetic `precision` (TACAW_DFT_*).
  * psi_k: DEVICE c64 [P][F][nq]; q_sel: DEVICE int32 [n_sel] ascending q indices to transform
  * (others are written as 0), or NULL for all nq; S_out: DEVICE float32 [P][F][nq] for
  * TACAW_REDUCE_NONE or [P][F] (sum over the selected q) for TACAW_REDUCE_DETECTOR. */
