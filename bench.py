@@ -130,25 +130,33 @@ def measured_peaks():
         "of fallback"
 
 
-def src_hash():
+# the sources each profiled kernel class is compiled from (device code, launch configuration
+# constants and tuning table); a class not listed hashes every CUDA source
+KERNEL_SOURCES = {k: ("k_slices.cu", "fft.cuh", "tacaw_internal.cuh", "tuning_table.h")
+                  for k in ("slice_row", "slice_col", "splat_row", "col_pot", "row_pot_t", "row_vt", "col_t",
+                            "row_tout", "sort_rows", "bin")}
+
+
+def src_hash(kernel=None):
+    """Hash of the CUDA sources the kernel class is built from (all of them if unlisted)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_10064_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel) or [f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
+    for f in sorted(files):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel, config, alg_bytes_per_launch):
     """DRAM bytes per launch from the committed ncu summary (profiles/traffic.md): the captured
     ratio of DRAM to algorithmic bytes times this run's algorithmic bytes per launch, if the
-    row matches the config, the kernel class and the current CUDA sources; else None."""
+    row matches the config, the kernel class and the current sources of that kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
     for line in open(p):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) == 5 and cells[0] == config and cells[1] == kernel and cells[4] == src_hash():
+        if len(cells) == 5 and cells[0] == config and cells[1] == kernel and cells[4] == src_hash(kernel):
             try:
                 return float(cells[2]) * alg_bytes_per_launch
             except ValueError:

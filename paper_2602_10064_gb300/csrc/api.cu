@@ -795,7 +795,7 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
   GeoCache* g;
   TRY_RC(get_geo(ctx, p, &g));
   Scratch sc(st);
-  const int P = pr.n_probes, S = p.n_slices;
+  const int P = pr.n_probes;
   const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
   int8_t* slots;
   TRY_RC(make_slots(ctx, Z, A, z_dev, true, sc, &slots));

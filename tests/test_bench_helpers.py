@@ -16,12 +16,21 @@ def test_traffic_scales_with_the_launch_and_needs_matching_sources(monkeypatch, 
         "|---|---|---|---|---|\n"
         "| c2 | slice_row | 1.25 | one launch | abc123 |\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "src_hash", lambda: "abc123")
+    monkeypatch.setattr(bench, "src_hash", lambda kernel=None: "abc123")
     assert bench.ncu_traffic("slice_row", "c2", 1000.0) == 1250.0
     assert bench.ncu_traffic("slice_col", "c2", 1000.0) is None
     assert bench.ncu_traffic("slice_row", "c4", 1000.0) is None
-    monkeypatch.setattr(bench, "src_hash", lambda: "changed")
+    monkeypatch.setattr(bench, "src_hash", lambda kernel=None: "changed")
     assert bench.ncu_traffic("slice_row", "c2", 1000.0) is None
+
+
+def test_src_hash_follows_only_the_kernels_sources():
+    """The FFT pass classes hash the files they are compiled from; host-side or time-transform
+    files do not enter their hash, and an unlisted class hashes every CUDA source."""
+    assert bench.src_hash("slice_row") == bench.src_hash("slice_col")
+    assert bench.src_hash("slice_row") != bench.src_hash(None)
+    assert "api.cu" not in bench.KERNEL_SOURCES["slice_row"]
+    assert "k_slices.cu" in bench.KERNEL_SOURCES["slice_row"]
 
 
 def test_roofline_picks_the_dominant_kernel_and_its_bound(monkeypatch):
