@@ -45,3 +45,32 @@ def test_roofline_picks_the_dominant_kernel_and_its_bound(monkeypatch):
     prof = {"dft_tc_bf16": (10.0, 1.0, 1e6, 5e11)}  # 5e11 flops in 10 ms
     r = bench.roofline(prof, 1, "c4", 2070.0)
     assert r["bound"] == "tensor" and abs(r["achieved"] - 50.0) < 1e-9 and abs(r["frac"] - 0.5) < 1e-12
+
+
+def _reference_line(env_extra=None):
+    import json
+    import subprocess
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c1",
+                        "--steps", "2", "--warmup", "1", "--ref-frames", "2"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm times the FP64 oracle on the host (no GPU) and prints one JSON line
+    with the same metric, unit and workload as the CUDA arm."""
+    (d,) = _reference_line()
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("c1-") and d["config"]["config"] == "c1"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "2 frame(s) per step" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the oracle and prints; the other ranks exit 0."""
+    assert _reference_line({"RANK": "1", "WORLD_SIZE": "2"}) == []
