@@ -469,6 +469,68 @@ def test_defocus_is_free_propagation():
     assert abs(np.sum(np.abs(oracle.probe_aberrated(p, 25.0, cs_mm=1.2, a1=40.0, phi_a=0.3)) ** 2) - 1) < 1e-12
 
 
+def _unitary_k(psi):
+    return oracle.fft2(psi, -1) / math.sqrt(psi.size)
+
+
+def _aperture_coefficients(N, L, alpha_mrad, lam):
+    """Focused aperture in k-space (uniform amplitude inside alpha/lambda) and the k grid."""
+    k = np.fft.fftfreq(N, d=L / N)
+    KX, KY = np.meshgrid(k, k, indexing="xy")  # KX[iy, ix] = k[ix]
+    inside = KX ** 2 + KY ** 2 <= (alpha_mrad * 1e-3 / lam) ** 2
+    return KX, KY, inside
+
+
+@pytest.mark.parametrize("a1,df", [(40.0, 0.0), (-25.0, 15.0)])
+def test_astigmatism_is_separable_fresnel_along_the_axes(a1, df):
+    # With phi_a = 0, a1 cos(2 phi) k^2 = a1 (kx^2 - ky^2): the probe equals the focused probe
+    # propagated by exp(-i pi lambda (df + a1) kx^2) along x and exp(-i pi lambda (df - a1) ky^2)
+    # along y.  A cos(phi) in place of cos(2 phi), or a flipped sign of a1, fails this.
+    N, L = 64, 16.0
+    p = oracle.params(N, N, 1, (L, L, 2.0), bandlimit=0.0)
+    lam = oracle.wavelength(100e3)
+    KX, KY, inside = _aperture_coefficients(N, L, 28.0, lam)
+    focused = _unitary_k(oracle.probe(p, 28.0, 2.5, 4.0))
+    want = focused * np.exp(-1j * np.pi * lam * ((df + a1) * KX ** 2 + (df - a1) * KY ** 2))
+    got = _unitary_k(oracle.probe_aberrated(p, 28.0, 2.5, 4.0, df=df, a1=a1, phi_a=0.0))
+    assert np.abs(got - want).max() < 1e-12
+    # the astigmatic phase is far from negligible at the aperture edge
+    assert np.pi * lam * abs(a1) * (28e-3 / lam) ** 2 > 1.0
+
+
+@pytest.mark.parametrize("phi_a", [np.pi / 4, 0.3])
+def test_astigmatism_rotated_axes_cartesian_form(phi_a):
+    # a1 cos 2(phi - phi_a) k^2 = a1 [cos(2 phi_a) (kx^2 - ky^2) + sin(2 phi_a) 2 kx ky]
+    N, L, a1 = 64, 16.0, 30.0
+    p = oracle.params(N, N, 1, (L, L, 2.0), bandlimit=0.0)
+    lam = oracle.wavelength(100e3)
+    KX, KY, inside = _aperture_coefficients(N, L, 28.0, lam)
+    focused = _unitary_k(oracle.probe(p, 28.0))
+    chi = np.pi * lam * a1 * (np.cos(2 * phi_a) * (KX ** 2 - KY ** 2) + np.sin(2 * phi_a) * 2 * KX * KY)
+    got = _unitary_k(oracle.probe_aberrated(p, 28.0, a1=a1, phi_a=phi_a))
+    assert np.abs(got - focused * np.exp(-1j * chi)).max() < 1e-12
+
+
+@pytest.mark.parametrize("cs_mm", [0.5, 1.2, -0.8])
+def test_spherical_aberration_textbook_angular_form(cs_mm):
+    # The spherical-aberration phase in angular form: chi(theta) = pi Cs theta^4 / (2 lambda),
+    # theta = lambda |k|, Cs converted from mm to A (1 mm = 1e7 A).  Compare the phase of every
+    # k inside the aperture of a centred probe with it.  lambda^2 in place of lambda^3, or a
+    # wrong mm -> A factor, fails this.
+    N, L, alpha = 96, 24.0, 30.0
+    p = oracle.params(N, N, 1, (L, L, 2.0), bandlimit=0.0)
+    lam = oracle.wavelength(100e3)
+    KX, KY, inside = _aperture_coefficients(N, L, alpha, lam)
+    theta = lam * np.sqrt(KX ** 2 + KY ** 2)
+    chi = np.pi * (cs_mm * 1e7) * theta ** 4 / (2.0 * lam)
+    got = _unitary_k(oracle.probe_aberrated(p, alpha, cs_mm=cs_mm))
+    amp = 1.0 / math.sqrt(inside.sum())
+    assert np.abs(got[inside] - amp * np.exp(-1j * chi[inside])).max() < 1e-11
+    assert np.abs(got[~inside]).max() < 1e-12
+    # at the aperture edge the phase spans many radians, so each factor is tested
+    assert np.abs(chi[inside]).max() / abs(cs_mm) > 50.0
+
+
 def test_multislice_from_initial_waves_matches_probe_path():
     w = workloads.diamond_si(n_frames=1, grid=32, n_slices=3)
     p = oracle.params_of(w)
