@@ -160,15 +160,54 @@ void oracle_dft2_brute(const cplx *in, cplx *out, int ny, int nx, int sign) {
 
 static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-/* In-place unnormalised radix-2 FFT (power-of-two n); sign -1 forward, +1 inverse.
- * Falls back to the direct DFT for other n.  Twiddles from cos/sin of the exact angle. */
+static int smallest_factor(int n) {
+    for (int p = 2; p * p <= n; p++)
+        if (n % p == 0) return p;
+    return n;
+}
+
+/* Mixed-radix decimation in time (Cooley-Tukey with the smallest prime factor p of n):
+ * with m = n / p and y_r the length-m transform of the samples x[p j + r], r = 0..p-1,
+ *   X[k + m q] = sum_r exp(sign 2 pi i r (k + m q) / n) y_r[k],   k < m, q < p.
+ * A prime n reduces to the direct sum.  w[j * ws] = exp(sign 2 pi i j / n) is the twiddle
+ * table of this length (a sub-transform of length m reads it with stride ws * p).  scratch
+ * holds 2 n values: y in the first n, the sub-transforms' own scratch after it. */
+static void fft_mixed(cplx *x, int n, const cplx *w, long ws, cplx *scratch) {
+    if (n <= 1) return;
+    const int p = smallest_factor(n), m = n / p;
+    cplx *y = scratch;  /* y[r m + k] = y_r[k] */
+    for (int r = 0; r < p; r++) {
+        for (int j = 0; j < m; j++) y[(size_t)r * m + j] = x[(size_t)j * p + r];
+        fft_mixed(y + (size_t)r * m, m, w, ws * p, scratch + n);
+    }
+    for (int q = 0; q < p; q++)
+        for (int k = 0; k < m; k++) {
+            const int kk = k + m * q;
+            cplx acc = 0;
+            long ph = 0;  /* r kk mod n, stepped by kk */
+            for (int r = 0; r < p; r++) {
+                acc += y[(size_t)r * m + k] * w[ph * ws];
+                ph += kk;
+                if (ph >= n) ph -= n;
+            }
+            x[kk] = acc;
+        }
+}
+
+/* In-place unnormalised FFT; sign -1 forward, +1 inverse.  Powers of two take the radix-2
+ * path below, every other n the mixed-radix one.  Twiddles from cos/sin of the exact angle. */
 void oracle_fft(cplx *x, int n, int sign) {
     if (n <= 1) return;
     if (!is_pow2(n)) {
-        cplx *tmp = malloc(sizeof(cplx) * (size_t)n);
-        oracle_dft(x, tmp, n, sign);
-        memcpy(x, tmp, sizeof(cplx) * (size_t)n);
-        free(tmp);
+        cplx *w = malloc(sizeof(cplx) * (size_t)n);
+        for (int j = 0; j < n; j++) {
+            double a = 2.0 * M_PI * (double)j / (double)n;
+            w[j] = cos(a) + sign * I * sin(a);
+        }
+        cplx *scratch = malloc(sizeof(cplx) * 2 * (size_t)n);
+        fft_mixed(x, n, w, 1, scratch);
+        free(scratch);
+        free(w);
         return;
     }
     for (int i = 1, j = 0; i < n; i++) {

@@ -30,6 +30,15 @@ def test_fft_equals_brute_force_dft(n, sign):
     assert rel(oracle.fft(x, sign), oracle.dft(x, sign)) < 1e-12
 
 
+@pytest.mark.parametrize("n", [6, 7, 9, 15, 45, 96, 100, 192, 384, 768, 1152])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_mixed_radix_fft_equals_brute_force_dft(n, sign):
+    # the lengths 3 * 2^k and 9 * 2^7 of the grids, plus odd and prime lengths
+    rng = np.random.default_rng(1000 + n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    assert rel(oracle.fft(x, sign), oracle.dft(x, sign)) < 1e-12
+
+
 def test_brute_dft_definition_small():
     # n = 4, forward: the matrix exp(-2 pi i jk/4) has entries 1, -i, -1, i.
     x = np.array([1.0, 2.0, 3.0, 4.0], dtype=complex)
@@ -37,7 +46,7 @@ def test_brute_dft_definition_small():
     assert np.abs(oracle.dft(x, -1) - want).max() < 1e-13
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (8, 16), (16, 4)])
+@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (8, 16), (16, 4), (12, 24), (24, 9)])
 def test_fft2_equals_brute_force_2d(shape):
     rng = np.random.default_rng(sum(shape))
     x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
