@@ -4,8 +4,6 @@
 // call needs no context and makes no allocation; the caller passes only its input and output.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/tacaw.h"
 #include "tacaw_internal.cuh"
 
@@ -16,25 +14,15 @@ namespace {
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up once per device: the
-// host-side symbol is only a stand-in and must never be handed to a kernel).
+// Device address of g_static_scratch in the current context.  The host-side symbol is only
+// a stand-in and must never be handed to a kernel.  The address is looked up on every call
+// (the lookup allocates nothing): a cached value would go stale when the context it was taken
+// in is replaced (cudaDeviceReset, or another context made current on the same device).
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -49,13 +37,16 @@ __global__ void k_static_time_twiddles(float2* tw, int64_t F) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool is_device(const void* p) {
+// True for device (or managed) memory of device `dev`, the current device: memory of another
+// GPU is rejected rather than handed to the kernels as a peer address.
+bool is_device(const void* p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -66,7 +57,9 @@ extern "C" int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, i
   using namespace tacaw;
   if (!psi_k || !S_out || P < 1 || F < 1 || nq < 1) return TACAW_EINVAL;
   if (P > 65535 || F > 65535) return TACAW_EINVAL;
-  if (!is_device(psi_k) || !is_device(S_out)) return TACAW_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TACAW_ECUDA;
+  if (!is_device(psi_k, dev) || !is_device(S_out, dev)) return TACAW_EINVAL;
   const size_t off_mean = align256((size_t)F * sizeof(float2));
   const size_t off_r = align256(off_mean + (size_t)P * nq * sizeof(double2));
   const double need = (double)off_r + (double)P * F * nq * sizeof(float2);
