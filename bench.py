@@ -2,9 +2,11 @@
 """Benchmark of the TACAW hot path (multislice + time transform) on one node.
 
 One step = the whole hot path for one synthetic trajectory: slice binning, projected
-potential, transmission, multislice for every (probe, frame), FP64 mean/residual, time
+potential, transmission, multislice for every (probe, frame), FP64-class mean/residual, time
 transform and |.|^2, through tacaw_run on device-resident inputs.  The default workload is
-the plane-wave rocksalt trajectory (8000 atoms, 1024 frames at 5 fs, 512^2, 20 slices).
+the largest single-GPU configuration, the probe scan: a 30 mrad probe on a 16 x 16 grid of
+positions over 576 diamond-cubic atoms, 256 frames at 5 fs, 256^2, 20 slices (65,536 waves);
+probe scans return the detector-summed spectrum image, plane waves the full S(q, w).
 With N ranks (torchrun) every rank runs its own independently seeded trajectory (weak
 scaling, no collective on the data path); value = all ranks' wave-slice steps / max time.
 
@@ -56,11 +58,16 @@ def make_workload(name, seed_offset=0, frames=None):
     return w
 
 
+def reduce_of(w):
+    """Probe scans return the spectrum image (detector sum), plane waves the full S."""
+    return "detector" if w.alpha_mrad > 0 else "none"
+
+
 def workload_config(w, name, precision):
     return {"workload": w.name, "config": name, "atoms": int(w.n_atoms), "frames": int(w.n_frames),
             "grid": [int(w.ny), int(w.nx)], "slices": int(w.n_slices), "probes": int(w.n_probes),
             "alpha_mrad": float(w.alpha_mrad), "dt_fs": float(w.dt_fs), "voltage_kev": w.voltage_ev / 1e3,
-            "bandlimit": "2/3", "time_transform": precision,
+            "bandlimit": "2/3", "time_transform": precision, "output": reduce_of(w),
             "l2": "256 MiB buffer written between timed steps (and each step streams > 3 GB)"}
 
 
@@ -221,26 +228,39 @@ def aggregate_ranks(local_seconds, local_units, dist=None):
 # CPU baseline (the FP64 oracle as it stands) on a bounded sample
 # ------------------------------------------------------------------------------------------
 def cpu_baseline(w, budget_s=20.0):
+    """The oracle on a bounded sample of the workload: frames in parallel (one per thread) and,
+    for a probe scan, the first probes of the scan; rate = wave-slice steps of the sample / time."""
     import numpy as np
 
     import oracle
     oracle.build()
     p = oracle.params_of(w)
-    probes = w.probes if w.alpha_mrad > 0 else None
-    t0 = time.perf_counter()
-    one = oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
-    t1 = time.perf_counter() - t0
     threads = oracle.num_threads()
-    # frames run in parallel (one per thread): n frames take about ceil(n / threads) * t1
-    n = max(1, min(w.n_frames, threads * max(1, int(budget_s / max(t1, 1e-3)))))
+    scan = w.alpha_mrad > 0
+    t0 = time.perf_counter()
+    oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, w.probes[:1] if scan else None)
+    t1 = time.perf_counter() - t0
+    # frames run in parallel (one per thread): n frames take about ceil(n / threads) frame times
+    if scan:
+        # a frame's time is its potential plus k probe propagations: calibrate both parts
+        t0 = time.perf_counter()
+        oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, w.probes[:3])
+        per_probe = max((time.perf_counter() - t0 - t1) / 2, 1e-3)
+        fixed = max(t1 - per_probe, 0.0)
+        n = min(w.n_frames, threads)
+        k = max(1, min(w.n_probes, int((budget_s - fixed) / per_probe)))
+    else:
+        n, k = max(1, min(w.n_frames, threads * max(1, int(budget_s / max(t1, 1e-3))))), 1
+    probes = w.probes[:k] if scan else None
     t0 = time.perf_counter()
     psi = oracle.multislice(p, w.pos[:n], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
-    S = oracle.spectrum(psi)
+    oracle.spectrum(psi)
     dt = time.perf_counter() - t0
-    units = n * w.n_slices * w.n_probes
-    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} of {w.n_frames} frames x {w.n_probes} probe(s) x {w.n_slices} slices, "
-                      f"multislice + time transform of those frames, {dt:.1f} s"}, psi, n
+    units = n * w.n_slices * k
+    what = (f"{n} of {w.n_frames} frames x {k} of {w.n_probes} probe(s) x {w.n_slices} slices, multislice + "
+            f"time transform of that sample, {dt:.1f} s; the rate is extrapolated to the whole workload")
+    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": what,
+            "extrapolated": True}, psi, n, probes
 
 
 # ------------------------------------------------------------------------------------------
@@ -260,13 +280,17 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle.multislice(p, w.pos[:1], w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
     times = []
+    # a probe scan times the first ref_probes probes of the scan per step (the rate is per wave)
+    if probes is not None:
+        probes = probes[:max(1, int(args.ref_probes))]
+    n_pr = 1 if probes is None else len(probes)
     for k in range(args.steps):
         fr = w.pos[(k * per_step) % w.n_frames:][:per_step]
         t0 = time.perf_counter()
         psi = oracle.multislice(p, fr, w.Z, w.form_Z, w.form_coef, w.alpha_mrad, probes)
         oracle.spectrum(psi)
         times.append(time.perf_counter() - t0)
-    units = per_step * w.n_slices * w.n_probes * args.steps
+    units = per_step * w.n_slices * n_pr * args.steps
     tot = sum(times)
     v = units / tot
     print(json.dumps({
@@ -275,37 +299,50 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(w, args.workload, "fp64 oracle"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"{per_step} frame(s) per step of {w.n_frames}, multislice + time transform"},
+                         "sample": f"{per_step} frame(s) x {n_pr} probe(s) per step of {w.n_frames} frames x "
+                                   f"{w.n_probes} probe(s), multislice + time transform"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 # ------------------------------------------------------------------------------------------
 # serving: Poisson-arriving requests, continuous batching vs the plain path
 # ------------------------------------------------------------------------------------------
+# the small mix of the default bench line; the serving configuration itself (--workload c5)
+# draws from its full stated ranges (workloads.request_stream defaults: grids 128^2-1024^2,
+# 64-1024 frames, 8-40 slices, 2-13 cubic cells per edge, plane waves or 4x4-16x16 scans)
 SERVING_MIX = dict(grids=(128, 256, 512), frames=(64, 128, 256), slices=(8, 20), reps=(2, 5), scans=(2, 4),
                    p_plane=0.5)
+FULL_MIX = dict(grids=(128, 256, 512, 1024), frames=(64, 128, 256, 512, 1024), slices=(8, 40), reps=(2, 13),
+                scans=(4, 16), p_plane=0.5)
 
 
-def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0):
+def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm=True, plain_sample=None):
     """Serve n_requests seeded requests arriving as a Poisson stream at rate_factor x the
-    measured batched capacity; compare with the same requests one by one on the plain path.
-    Plane-wave requests return the full S, probe scans the detector-summed spectrum image."""
+    measured batched capacity; compare with the plain path (requests one by one).  Plane-wave
+    requests return the full S, probe scans the detector-summed spectrum image.
+    mix: request ranges (SERVING_MIX or FULL_MIX); warm: run every request once first (tables,
+    operands, pools); plain_sample: time the plain path on a seeded sample of that many requests
+    and extrapolate it to the whole stream by pixel-slice work (None: every request)."""
     import numpy as np
     import torch
 
     import workloads
-    specs = workloads.request_stream(n_requests, seed=seed, rate_hz=1.0, **SERVING_MIX)
+    mix = SERVING_MIX if mix is None else mix
+    specs = workloads.request_stream(n_requests, seed=seed, rate_hz=1.0, **mix)
     ws = [workloads.request_workload(sp) for sp in specs]
     fz, fc = workloads.placeholder_form_factors(sorted(set(int(z) for w in ws for z in w.Z)))
-    ctx = T.Context(device)
-    ctx.load_form_factors(fz, fc)
     reqs = []
     for w in ws:
         red = T.REDUCE_NONE if w.alpha_mrad <= 0 else T.REDUCE_DETECTOR
         shape = (w.n_probes, w.n_frames, w.ny, w.nx) if red == T.REDUCE_NONE else (w.n_probes, w.n_frames)
         reqs.append(dict(w=w, red=red, pos=torch.from_numpy(w.pos).cuda(), Z=np.ascontiguousarray(w.Z),
                          out=torch.empty(shape, dtype=torch.float32, device="cuda"), pr=T.probe_of(w)))
-    units = sum(r["w"].n_probes * r["w"].n_frames * r["w"].n_slices for r in reqs)
+    # the context after the request buffers: its serving budget is 90% of the memory left
+    ctx = T.Context(device)
+    ctx.load_form_factors(fz, fc)
+    work = lambda r: r["w"].n_probes * r["w"].n_frames * r["w"].n_slices
+    pxwork = lambda r: work(r) * r["w"].nx * r["w"].ny
+    units = sum(work(r) for r in reqs)
     spectra = sum(r["w"].n_probes for r in reqs)
 
     def one(r, prec):
@@ -325,7 +362,7 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0):
             tickets.append(T.tacaw_submit(ctx.h, req))
         lat, first, last = [], None, None
         for t in tickets:
-            rc, res = T.tacaw_wait(ctx.h, t, 600.0)
+            rc, res = T.tacaw_wait(ctx.h, t, 3600.0)
             if rc != T.TACAW_OK:
                 raise RuntimeError(f"serving request failed: {rc}")
             lat.append(res.t_done - res.t_submit)
@@ -333,22 +370,28 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0):
             last = res.t_done if last is None else max(last, res.t_done)
         return lat, last - first
 
-    # warm every geometry and both transforms once (tables, operands, pools)
-    for r in reqs:
-        one(r, T.DFT_BF16X3)
-        one(r, T.DFT_FP32)
-    torch.cuda.synchronize()
+    if warm:
+        for r in reqs:
+            one(r, T.DFT_BF16X3)
+            one(r, T.DFT_FP32)
+        torch.cuda.synchronize()
     # plain path: one frame per launch batch, FP32 SIMT transform, one request at a time
+    if plain_sample is None or plain_sample >= len(reqs):
+        sample = list(range(len(reqs)))
+    else:
+        sample = sorted(np.random.default_rng(seed).choice(len(reqs), plain_sample, replace=False).tolist())
     ctx.set_option("max_chunk_frames", 1)
     plain_lat = []
     t0 = time.perf_counter()
-    for r in reqs:
+    for i in sample:
         a = time.perf_counter()
-        one(r, T.DFT_FP32)
+        one(reqs[i], T.DFT_FP32)
         torch.cuda.synchronize()
         plain_lat.append(time.perf_counter() - a)
-    plain_s = time.perf_counter() - t0
+    plain_sample_s = time.perf_counter() - t0
     ctx.set_option("max_chunk_frames", 0)
+    extrap = len(sample) < len(reqs)
+    plain_s = plain_sample_s * (sum(pxwork(r) for r in reqs) / sum(pxwork(reqs[i]) for i in sample))
     # batched capacity: everything submitted at once
     _, cap_s = serve(T.DFT_BF16X3, [0.0] * len(reqs))
     rate = rate_factor * len(reqs) / cap_s
@@ -357,19 +400,24 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0):
     ctx.check()
     ctx.close()
     pct = lambda x, q: float(np.percentile(np.asarray(x), q))
+    plain_what = "requests one by one: one frame per launch batch, FP32 SIMT time transform"
+    if extrap:
+        plain_what += (f"; timed on a seeded sample of {len(sample)} of {len(reqs)} requests "
+                       f"({plain_sample_s:.1f} s) and extrapolated by pixel-slice work")
     return {
         "requests": len(reqs), "spectra": spectra, "wave_slice_steps": units,
-        "mix": {k: list(v) if isinstance(v, tuple) else v for k, v in SERVING_MIX.items()},
+        "mix": {k: list(v) if isinstance(v, tuple) else v for k, v in mix.items()},
         "arrival_rate_hz": rate, "offered_load": rate_factor,
         "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
         "spectra_per_s": spectra / span, "wave_slice_steps_per_s": units / span,
         "batched_capacity_spectra_per_s": spectra / cap_s,
         "plain_path": {"spectra_per_s": spectra / plain_s, "wave_slice_steps_per_s": units / plain_s,
                        "p50_latency_s": pct(plain_lat, 50), "p99_latency_s": pct(plain_lat, 99),
-                       "what": "same requests one by one: one frame per launch batch, FP32 SIMT time transform"},
+                       "latencies_from": f"{len(sample)} requests", "extrapolated": extrap, "what": plain_what},
         "capacity_speedup_vs_plain": (spectra / cap_s) / (spectra / plain_s),
         "served_rate_vs_plain": (spectra / span) / (spectra / plain_s),
         "precision": "bf16x3 served, fp32 plain (both within 1e-4 of the oracle in the tests)",
+        "warmed": warm,
     }
 
 
@@ -382,14 +430,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m1"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "m1"])
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-frames", type=int, default=0, help="frames per reference step (0: one per host thread)")
+    ap.add_argument("--ref-probes", type=int, default=2, help="probes of a scan per reference step")
     ap.add_argument("--frames", type=int, default=None, help="truncate the trajectory (profiling cases)")
     ap.add_argument("--serving-requests", type=int, default=24, help="requests in the serving run (0: skip)")
+    ap.add_argument("--plain-sample", type=int, default=16,
+                    help="c5: requests of the stream the plain path is timed on (0: all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -422,12 +473,14 @@ def main():
     pos = torch.from_numpy(w.pos).cuda()
     Z = torch.from_numpy(w.Z).cuda()
     P, F = w.n_probes, w.n_frames
-    S = torch.empty((P, F, w.ny, w.nx), dtype=torch.float32, device="cuda")
+    red = T.REDUCE_DETECTOR if reduce_of(w) == "detector" else T.REDUCE_NONE
+    out_shape = (P, F) if red == T.REDUCE_DETECTOR else (P, F, w.ny, w.nx)
+    S = torch.empty(out_shape, dtype=torch.float32, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
     def step():
-        T.tacaw_run(ctx.h, params, pos, Z, w.n_atoms, F, probe, prec, T.REDUCE_NONE, S, stream)
+        T.tacaw_run(ctx.h, params, pos, Z, w.n_atoms, F, probe, prec, red, S, stream)
 
     for _ in range(args.warmup):
         step()
@@ -471,8 +524,8 @@ def main():
         args.e2e_steps = 0
     pos_h = torch.from_numpy(w.pos).pin_memory()
     Z_h = torch.from_numpy(w.Z)
-    S_h = torch.empty((P, F, w.ny, w.nx), dtype=torch.float32).pin_memory()
-    T.tacaw_run(ctx.h, params, pos_h, Z_h, w.n_atoms, F, probe, prec, T.REDUCE_NONE, S_h, stream)
+    S_h = torch.empty(out_shape, dtype=torch.float32).pin_memory()
+    T.tacaw_run(ctx.h, params, pos_h, Z_h, w.n_atoms, F, probe, prec, red, S_h, stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -480,7 +533,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(max(args.e2e_steps, 1)):
         t1 = time.perf_counter()
-        T.tacaw_run(ctx.h, params, pos_h, Z_h, w.n_atoms, F, probe, prec, T.REDUCE_NONE, S_h, stream)
+        T.tacaw_run(ctx.h, params, pos_h, Z_h, w.n_atoms, F, probe, prec, red, S_h, stream)
         call_ms.append((time.perf_counter() - t1) * 1e3)  # the call returns once S is on the host
     torch.cuda.synchronize()
     e2e_value, _ = aggregate_ranks(time.perf_counter() - t0, units_rank // args.steps * max(args.e2e_steps, 1), dist)
@@ -515,13 +568,14 @@ def main():
     if world == 1 and args.serving_requests > 0:
         out["serving"] = run_serving(T, args.serving_requests, device=local)
     if world == 1 and not args.no_cpu_baseline:
-        cb, psi_ref, n = cpu_baseline(w, args.cpu_seconds)
+        cb, psi_ref, n, probes_s = cpu_baseline(w, args.cpu_seconds)
         out["cpu_baseline"] = cb
-        # the same frames on the GPU: exit-wave agreement at full size
+        # the same frames (and probes) on the GPU: exit-wave agreement at full size
         V = ctx.build_potential(params, pos[:n].contiguous(), Z)
-        psi = ctx.propagate(params, V, probe).cpu().numpy()
+        pr_s = probe if probes_s is None else T.ProbeSpec(w.alpha_mrad, probes_s)
+        psi = ctx.propagate(params, V, pr_s).cpu().numpy()
         err = float(np.linalg.norm(psi - psi_ref) / np.linalg.norm(psi_ref))
-        out["tol"] = {"psi_rel_l2_vs_oracle": err, "frames": n,
+        out["tol"] = {"psi_rel_l2_vs_oracle": err, "frames": n, "probes": 1 if probes_s is None else len(probes_s),
                       "S_rel_l2_bound": "1e-4 (tests/test_gpu_parity.py at oracle sizes)"}
     ctx.close()
     print(json.dumps(out))
@@ -538,7 +592,8 @@ def main_serving(args, rank, world, local):
     n = args.serving_requests if args.serving_requests > 24 else 200
     clocks = ClockSampler(local)
     clocks.start()
-    r = run_serving(T, n, seed=5 + 1000 * rank, device=local)
+    r = run_serving(T, n, seed=5 + 1000 * rank, device=local, mix=FULL_MIX, warm=False,
+                    plain_sample=args.plain_sample or None)
     clk = clocks.stop()
     if rank != 0:
         return
@@ -547,7 +602,8 @@ def main_serving(args, rank, world, local):
         "warmup": 1, "ms_per_step": r["wave_slice_steps"] / r["wave_slice_steps_per_s"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic request stream (seeded cubic/rocksalt cells, Poisson arrivals)",
-        "config": {"workload": f"c5-serving-{n}-requests", "mix": r["mix"]}, "serving": r, "clocks": clk}))
+        "config": {"workload": f"c5-serving-{n}-requests", "mix": r["mix"]}, "serving": r, "clocks": clk,
+        "spectra_per_s": r["spectra_per_s"], "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"]}))
 
 
 if __name__ == "__main__":

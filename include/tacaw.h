@@ -92,6 +92,16 @@ typedef struct tacaw_probe {
 /* Library version string (static storage). */
 const char* tacaw_version(void);
 
+/* Sampling of a simulation (Supplement, "Sampling Considerations": reciprocal-space resolution
+ * dk = 1/L, reach k_max = 1/(2 dx); frequency resolution df = 1/(F dt), Nyquist f_max =
+ * 1/(2 dt)).  Host-only arithmetic, no context and no GPU.  Outputs (HOST, any may be NULL):
+ * kx [nx] and ky [ny], the spatial frequencies (1/A) of the grid in FFT order; f_thz [n_frames],
+ * the frequencies of the time-transform bins in FFT order (THz); sampling [6] = dk_x, dk_y,
+ * k_max_x, k_max_y (1/A), df, f_max (THz).  Uses nx, ny, cell[0..1] and dt_fs of params.
+ * EINVAL for sizes below 1 or non-positive lengths or dt. */
+int tacaw_axes(const tacaw_params* params, int64_t n_frames, double* kx, double* ky, double* f_thz,
+               double* sampling);
+
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
  * serving loop admits at once (0 = 90% of the device's free memory at creation).  *out
  * receives a library-owned handle, released by tacaw_destroy. */
@@ -217,6 +227,14 @@ typedef struct tacaw_result {
  * times.  *ticket identifies the request. */
 int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket);
 
+/* Device bytes the request would reserve while it runs (its admission footprint), without
+ * submitting it: *bytes is set and TACAW_OK returned if the request fits the context's budget,
+ * TACAW_ETOOBIG if it never can; EINVAL as tacaw_submit (the buffer pointers are not needed).
+ * A run bounds its scratch: probes are propagated and transformed in blocks, and a probe's
+ * exit-wave stack keeps only the in-band points, so a scan's footprint grows with the block,
+ * not with the number of probes. */
+int tacaw_request_footprint(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* bytes);
+
 /* TACAW_PENDING while the request is queued or running; otherwise its final status (TACAW_OK,
  * an error code, or TACAW_ECANCELED), after which the ticket is released.  out (optional)
  * receives the request's state.  TACAW_ENOTFOUND for unknown or released tickets. */
@@ -241,17 +259,21 @@ int tacaw_serving_stats(tacaw_ctx* ctx, int64_t* queued, int64_t* active, uint64
  * allocates) nor cudaMalloc / cudaFree / an allocating library routine is used.
  * It computes the same S as tacaw_spectrum(..., TACAW_DFT_FP32, TACAW_REDUCE_NONE, q_sel = NULL):
  * S[p][m][q] = |sum_n (psi[p][n][q] - mean_n psi[p][n][q]) exp(-2 pi i m n / F)|^2 with the mean
- * and residual in FP64 and the sum in FP32.
- * psi_k: DEVICE c64 [P][F][nq]; S_out: DEVICE float32 [P][F][nq]; stream as elsewhere.
+ * and the residual to FP64-class precision (FP32-pair sums and exact differences, combined in
+ * FP64 once per q) and the sum in FP32.
+ * psi_k: DEVICE c64 [P][F][nq]; S_out: DEVICE float32 [P][F][nq], both on the current device;
+ * stream as elsewhere.
  * Scratch (time twiddles, FP64 mean, residual: 8 F + 16 P nq + 8 P F nq bytes, each part
  * rounded up to 256 bytes) lives in a file-scope device array of 16 MiB that every GPU loading
  * the library holds until the process exits.  Larger problems return TACAW_ETOOBIG; P or F
- * above 65535, a NULL or non-device pointer, or a size below 1 return TACAW_EINVAL; a failed
- * launch returns TACAW_ECUDA.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any stream
- * capture.  Every call overwrites all the scratch it reads, so nothing carries over between
- * calls, but all calls share the one array: calls that overlap on the GPU (other streams,
- * other host threads) race and must be serialised by the caller. */
+ * above 65535, a NULL pointer, a pointer that is not device memory of the current device, or a
+ * size below 1 return TACAW_EINVAL; a failed launch returns TACAW_ECUDA.  Every call looks up
+ * the array's device address in the current context (cudaGetSymbolAddress, which allocates
+ * nothing); the first lookup in a context can load the library's device code, so make the
+ * first call on a device before any stream capture.  Every call overwrites all the scratch it
+ * reads, so nothing carries over between calls, but all calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be serialised by the
+ * caller. */
 int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, float* S_out, void* stream);
 
 /* Context option.  "max_chunk_frames": cap on the frames whose waves are propagated together
@@ -259,8 +281,10 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * plain frame-at-a-time path).  "max_slice_block": cap on the slices whose potentials and
  * transmission functions tacaw_run builds together for a chunk of frames (0 = automatic: all
  * S slices unless that would leave a slice launch with fewer than "min_wave_rows" wave rows,
- * default 65536).  Results do not depend on these options.  EINVAL for an unknown name or a
- * bad value. */
+ * default 65536).  "max_run_bytes": bound on the scratch of one run (0 = automatic: half the
+ * context's budget, at most 64 GiB); probes are propagated and transformed in blocks sized to
+ * it.  "max_probe_block": cap on the probes of one block (0 = no cap).  Results do not depend on
+ * these options.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 
 /* Wait for all work on the context's device, then report what the context's kernels flagged

@@ -117,6 +117,7 @@ def lib():
         pp, prp = C.POINTER(Params), C.POINTER(Probe)
         sig = {
             "tacaw_version": (C.c_char_p, []),
+            "tacaw_axes": (C.c_int, [pp, i64, vp, vp, vp, vp]),
             "tacaw_create": (C.c_int, [C.POINTER(vp), i32, C.c_uint64]),
             "tacaw_destroy": (C.c_int, [vp]),
             "tacaw_last_error": (C.c_char_p, [vp]),
@@ -136,6 +137,7 @@ def lib():
             "tacaw_accumulate": (C.c_int, [vp, vp, i64, C.c_double, vp, vp]),
             "tacaw_spectrum_static": (C.c_int, [vp, i64, i64, i64, vp, vp]),
             "tacaw_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+            "tacaw_request_footprint": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
             "tacaw_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
             "tacaw_wait": (C.c_int, [vp, C.c_uint64, C.c_double, C.POINTER(Result)]),
             "tacaw_cancel": (C.c_int, [vp, C.c_uint64]),
@@ -153,10 +155,10 @@ def lib():
 
 
 def exported_symbols():
-    return ["tacaw_version", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
+    return ["tacaw_version", "tacaw_axes", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
             "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
             "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_select", "tacaw_profile_end",
-            "tacaw_spectrum_static", "tacaw_submit", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
+            "tacaw_spectrum_static", "tacaw_submit", "tacaw_request_footprint", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
             "tacaw_serving_stats", "tacaw_set_option", "tacaw_spectral_diffraction", "tacaw_dispersion",
             "tacaw_accumulate", "tacaw_selftest_wait"]
 
@@ -259,6 +261,15 @@ def tacaw_submit(ctx, req: Request) -> int:
     t = C.c_uint64()
     _check(ctx, lib().tacaw_submit(ctx, C.byref(req), C.byref(t)))
     return t.value
+
+
+def tacaw_request_footprint(ctx, req: Request):
+    """(code, bytes): the device bytes the request would reserve; code TACAW_OK or TACAW_ETOOBIG."""
+    b = C.c_uint64()
+    rc = lib().tacaw_request_footprint(ctx, C.byref(req), C.byref(b))
+    if rc not in (TACAW_OK, TACAW_ETOOBIG):
+        _check(ctx, rc)
+    return rc, b.value
 
 
 def tacaw_poll(ctx, ticket):
@@ -447,19 +458,33 @@ class Context:
 
 
 # ------------------------------------------------------------------------------------------
-# axes (Supplement, "Sampling Considerations": dk = 1/L, df = 1/(N dt), f_max = 1/(2 dt))
+# axes (Supplement, "Sampling Considerations"), computed by tacaw_axes
 # ------------------------------------------------------------------------------------------
+def tacaw_axes(params, n_frames):
+    """(kx [nx], ky [ny], f_thz [F], sampling [6]) of a simulation: see include/tacaw.h."""
+    kx = np.zeros(params.nx)
+    ky = np.zeros(params.ny)
+    f = np.zeros(int(n_frames))
+    smp = np.zeros(6)
+    rc = lib().tacaw_axes(C.byref(params), int(n_frames), kx.ctypes.data, ky.ctypes.data, f.ctypes.data,
+                          smp.ctypes.data)
+    if rc != TACAW_OK:
+        raise TacawError(rc, "tacaw_axes: bad sizes, lengths or dt")
+    return kx, ky, f, smp
+
+
 def frequency_axis_thz(n_frames, dt_fs):
     """Frequencies of the time-transform bins in FFT order (THz): f_m = m / (F dt)."""
-    return np.fft.fftfreq(int(n_frames), d=float(dt_fs) * 1e-3)
+    return tacaw_axes(make_params(1, 1, 1, (1.0, 1.0, 1.0), dt_fs=dt_fs), n_frames)[2]
 
 
 def k_axis(n, L):
     """Spatial frequencies (cycles/A) of an n-point axis of length L, FFT order."""
-    return np.fft.fftfreq(int(n), d=float(L) / int(n))
+    return tacaw_axes(make_params(int(n), 1, 1, (float(L), 1.0, 1.0)), 1)[0]
 
 
-def sampling(L, sampling_A, n_frames, dt_fs):
-    """(dk, k_max, df, f_max) of a simulation: 1/L, 1/(2 dx), 1/(F dt), 1/(2 dt) (A^-1, THz)."""
-    dt_ps = float(dt_fs) * 1e-3
-    return 1.0 / L, 1.0 / (2.0 * sampling_A), 1.0 / (n_frames * dt_ps), 1.0 / (2.0 * dt_ps)
+def sampling(params, n_frames):
+    """(dk, k_max, df, f_max) along x of a simulation: 1/Lx, nx/(2 Lx) = 1/(2 dx), 1/(F dt),
+    1/(2 dt) (1/A and THz)."""
+    smp = tacaw_axes(params, n_frames)[3]
+    return float(smp[0]), float(smp[2]), float(smp[4]), float(smp[5])

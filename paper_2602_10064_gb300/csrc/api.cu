@@ -320,6 +320,20 @@ int get_geo(tacaw_ctx* ctx, const tacaw_params& p, GeoCache** out) {
   g->nsel = (int64_t)qs.size();
   TRY_RC(owned_alloc(ctx, &g->qsel, qs.size()));
   CK(cudaMemcpy(g->qsel, qs.data(), sizeof(int32_t) * qs.size(), cudaMemcpyHostToDevice));
+  // per-row start and count of the in-band points (the compact exit-wave layout), checked
+  // against the position rule the last column pass uses
+  std::vector<int2> disc(ny, make_int2(0, 0));
+  for (size_t i = 0; i < qs.size(); ++i) disc[qs[i] / nx].y++;
+  for (int y = 1; y < ny; ++y) disc[y].x = disc[y - 1].x + disc[y - 1].y;
+  for (size_t i = 0; i < qs.size(); ++i) {
+    const int y = qs[i] / nx, x = qs[i] % nx;
+    const int c = x <= mb ? x : x - nx + W, a = (disc[y].y - 1) >> 1;
+    const int j = disc[y].y == nx ? c : (c <= a ? c : c - W + 2 * a + 1);
+    if ((int64_t)disc[y].x + j != (int64_t)i)
+      return set_err(ctx, TACAW_EINVAL, "internal: in-band layout of row %d is not symmetric", y);
+  }
+  TRY_RC(owned_alloc(ctx, &g->disc, ny));
+  CK(cudaMemcpy(g->disc, disc.data(), sizeof(int2) * ny, cudaMemcpyHostToDevice));
   // potential multiplier table over the loaded species (slot = table index)
   const int nslot = (int)ctx->ffZ.size();
   if (nslot > 0) {
@@ -367,6 +381,31 @@ int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out) {
 extern "C" {
 
 const char* tacaw_version(void) { return "tacaw-gb300 0.1 (sm_103a)"; }
+
+int tacaw_axes(const tacaw_params* params, int64_t n_frames, double* kx, double* ky, double* f_thz,
+               double* sampling) {
+  if (!params || params->nx < 1 || params->ny < 1 || n_frames < 1) return TACAW_EINVAL;
+  const double Lx = params->cell[0], Ly = params->cell[1], dt_ps = params->dt_fs * 1e-3;
+  if (!(Lx > 0.0) || !(Ly > 0.0) || !(dt_ps > 0.0) || !std::isfinite(Lx) || !std::isfinite(Ly) ||
+      !std::isfinite(dt_ps))
+    return TACAW_EINVAL;
+  const int64_t F = n_frames;
+  if (kx)
+    for (int i = 0; i < params->nx; ++i) kx[i] = kfreq(i, params->nx, Lx);
+  if (ky)
+    for (int i = 0; i < params->ny; ++i) ky[i] = kfreq(i, params->ny, Ly);
+  if (f_thz)
+    for (int64_t m = 0; m < F; ++m) f_thz[m] = (double)(m < (F + 1) / 2 ? m : m - F) / ((double)F * dt_ps);
+  if (sampling) {
+    sampling[0] = 1.0 / Lx;
+    sampling[1] = 1.0 / Ly;
+    sampling[2] = 0.5 * (double)params->nx / Lx;
+    sampling[3] = 0.5 * (double)params->ny / Ly;
+    sampling[4] = 1.0 / ((double)F * dt_ps);
+    sampling[5] = 0.5 / dt_ps;
+  }
+  return TACAW_OK;
+}
 
 int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
   if (!out) return TACAW_EINVAL;
@@ -492,14 +531,15 @@ int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, bo
   return TACAW_OK;
 }
 
-// Potential of frames [0, nf): binning, then per chunk of `chunk` frames and per block of `sb`
-// slices the spreading row pass and the column pass.  Leaves Ap [nfc][sbc][ny][Wp] to
-// `sink(f0, nfc, s0, sbc, Ap)`, which runs the row pass out of the potential.
-template <class Sink>
-int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float* pos, const int8_t* slots,
-                     int64_t A, int64_t nf, int64_t chunk, int sb, Scratch& sc, Sink sink) {
-  const int S = p.n_slices, ny = p.ny;
-  const Geo geo{p.nx, p.ny, ctx->tw};
+// Binned atoms of frames [0, nf): per-(frame, slice) lists, then the row-sorted copy with the
+// offsets of every block of SPREAD_YB grid rows that the spreading pass reads.
+struct Binned {
+  AtomRec* rrecs = nullptr;
+  int* boffs = nullptr;
+};
+int bin_frames(tacaw_ctx* ctx, const tacaw_params& p, const float* pos, const int8_t* slots, int64_t A, int64_t nf,
+               Scratch& sc, Binned* out) {
+  const int S = p.n_slices, ny = p.ny, nyb = ny / SPREAD_YB;
   AtomRec* recs;
   int* offs;
   CK(sc.get(&recs, (size_t)nf * std::max<int64_t>(A, 1)));
@@ -509,41 +549,58 @@ int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const f
     ProfScope ps(ctx, "bin", sc.st, (double)nf * A * 28, 0);
     CK(launch_bin(pos, A, nf, S, p.cell[0], p.cell[1], p.cell[2], p.nx, p.ny, slots, recs, offs, nullptr, sc.st));
   }
-  AtomRec* rrecs;
-  int* boffs;
-  const int nyb = ny / SPREAD_YB;
-  CK(sc.get(&rrecs, (size_t)nf * std::max<int64_t>(A, 1)));
-  CK(sc.get(&boffs, (size_t)nf * S * (nyb + 1)));
+  CK(sc.get(&out->rrecs, (size_t)nf * std::max<int64_t>(A, 1)));
+  CK(sc.get(&out->boffs, (size_t)nf * S * (nyb + 1)));
   {
     NvtxRange r_sort("binning_rows");
     ProfScope ps(ctx, "sort_rows", sc.st, (double)nf * A * 48 + (double)nf * S * (nyb + 1) * 4, 0);
-    CK(launch_sort_rows(recs, offs, A, nf, S, ny, rrecs, boffs, sc.st));
+    CK(launch_sort_rows(recs, offs, A, nf, S, ny, out->rrecs, out->boffs, sc.st));
   }
-  float2 *Bp, *Ap;
-  const size_t plane = (size_t)ny * g->band.Wp;
-  CK(sc.get(&Bp, (size_t)chunk * sb * g->npair * plane));
-  CK(sc.get(&Ap, (size_t)chunk * sb * plane));
+  return TACAW_OK;
+}
+
+// Potential of slices [s0, s0 + sbc) of frames [f0, f0 + nfc): the spreading row pass into Bp
+// and the column pass into Ap [nfc][sbc][ny][Wp] (compact columns), for a row pass out of it.
+int potential_block(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const Binned& bn, int64_t A, int64_t f0,
+                    int nfc, int s0, int sbc, float2* Bp, float2* Ap, cudaStream_t st) {
+  const int S = p.n_slices, ny = p.ny, nyb = ny / SPREAD_YB, nfs = nfc * sbc;
+  const Geo geo{p.nx, p.ny, ctx->tw};
   const SpreadKernel sk{kSpreadHalf, (float)kSpreadBeta};
   const double W8 = (double)g->band.W * 8.0, fx = 5.0 * p.nx * std::log2((double)p.nx),
                fy = 5.0 * ny * std::log2((double)ny);
+  NvtxRange r_pot("potential");
+  {
+    ProfScope ps(ctx, "splat_row", st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
+                 (double)nfs * g->npair * ny * fx);
+    CK(launch_splat_row(geo, g->band, bn.rrecs + (size_t)f0 * A, bn.boffs + (size_t)f0 * S * (nyb + 1), A, S, s0,
+                        sbc, nfs, g->npair, sk, Bp, st));
+  }
+  {
+    ProfScope ps(ctx, "col_pot", st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
+                 (double)nfs * (g->npair + 1) * g->band.W * fy);
+    CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, st));
+  }
+  return TACAW_OK;
+}
+
+// Potential of frames [0, nf): binning, then per chunk of `chunk` frames and per block of `sb`
+// slices the spreading row pass and the column pass.  Leaves Ap [nfc][sbc][ny][Wp] to
+// `sink(f0, nfc, s0, sbc, Ap)`, which runs the row pass out of the potential.
+template <class Sink>
+int potential_chunks(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float* pos, const int8_t* slots,
+                     int64_t A, int64_t nf, int64_t chunk, int sb, Scratch& sc, Sink sink) {
+  const int S = p.n_slices;
+  Binned bn;
+  TRY_RC(bin_frames(ctx, p, pos, slots, A, nf, sc, &bn));
+  float2 *Bp, *Ap;
+  const size_t plane = (size_t)p.ny * g->band.Wp;
+  CK(sc.get(&Bp, (size_t)chunk * sb * g->npair * plane));
+  CK(sc.get(&Ap, (size_t)chunk * sb * plane));
   for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
     const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
     for (int s0 = 0; s0 < S; s0 += sb) {
-      const int sbc = std::min(sb, S - s0), nfs = nfc * sbc;
-      {
-        NvtxRange r_pot("potential");
-        {
-          ProfScope ps(ctx, "splat_row", sc.st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
-                       (double)nfs * g->npair * ny * fx);
-          CK(launch_splat_row(geo, g->band, rrecs + (size_t)f0 * A, boffs + (size_t)f0 * S * (nyb + 1), A, S, s0,
-                              sbc, nfs, g->npair, sk, Bp, sc.st));
-        }
-        {
-          ProfScope ps(ctx, "col_pot", sc.st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
-                       (double)nfs * (g->npair + 1) * g->band.W * fy);
-          CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, sc.st));
-        }
-      }
+      const int sbc = std::min(sb, S - s0);
+      TRY_RC(potential_block(ctx, p, g, bn, A, f0, nfc, s0, sbc, Bp, Ap, sc.st));
       TRY_RC(sink(f0, nfc, s0, sbc, Ap));
     }
   }
@@ -682,13 +739,15 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
   return TACAW_OK;
 }
 
-// Slices [s0, s0 + sb) of the multislice of nfc frames, whose transmission functions are
-// t[fl][s - s0][ny][nx] (or the compact [..][ny][Wp] with `tfused`); the waves carry over in
-// Apsi between calls, and the exit waves go to psi_k[p][f0 + fl] of a [P][F_total][ny][nx]
-// stack (zeroed by the caller) when the block holds the last slice.
-int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, int nfc, int s0, int sb, int P,
-           const float2* psi0, int64_t F_total, int64_t f0, float2* psi_k, Scratch& sc, float2* Apsi, float2* Bpsi,
-           bool tfused) {
+// Slices [s0, s0 + sb) of the multislice of nfc frames.  The transmission function of frame fl
+// and slice s is t[fl][s - t_first][ny][nx] of a buffer holding t_slices slices per frame (or
+// the compact [..][ny][Wp] with `tfused`).  The waves carry over in Apsi between calls, and the
+// exit waves go to psi_k[p][f0 + fl] of a [P][F_total] stack when the block holds the last
+// slice: full [ny][nx] planes (zeroed by the caller) or, with `compact`, the nsel in-band
+// points of each wave.
+int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, int t_slices, int t_first, int nfc,
+           int s0, int sb, int P, const float2* psi0, int64_t F_total, int64_t f0, float2* psi_k, bool compact,
+           Scratch& sc, float2* Apsi, float2* Bpsi, bool tfused) {
   const Geo geo{p.nx, p.ny, ctx->tw};
   const int S = p.n_slices;
   const float nq = (float)p.nx * (float)p.ny;
@@ -700,26 +759,24 @@ int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, 
     {
       const double in = s > 0 ? W8 : (psi0 ? 8.0 * p.nx : 0.0), tin = tfused ? W8 : 8.0 * p.nx;
       ProfScope ps(ctx, "slice_row", sc.st, rows * (in + tin + W8), rows * ((s > 0 ? 2 : 1) + (tfused ? 1 : 0)) * fx);
-      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, tfused, Apsi, psi0, t, sb, s - s0, P, nfc,
-                          plane_amp, Bpsi, sc.st));
+      CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, tfused, Apsi, psi0, t, t_slices, s - t_first, P,
+                          nfc, plane_amp, Bpsi, sc.st));
     }
     {
-      ProfScope ps(ctx, "slice_col", sc.st, rows * 2 * W8, (double)P * nfc * g->band.W * (last ? 1 : 2) * fy);
+      const double out = last && compact ? (double)g->nsel * 8.0 * P * nfc : rows * W8;
+      ProfScope ps(ctx, "slice_col", sc.st, rows * W8 + out, (double)P * nfc * g->band.W * (last ? 1 : 2) * fy);
       CK(launch_slice_col(geo, g->band, last, Bpsi, g->px, g->py,
                           last ? (float)(1.0 / std::sqrt((double)p.nx * p.ny)) : 1.0f / nq, P, nfc, F_total, f0,
-                          Apsi, psi_k, sc.st));
+                          compact ? g->disc : nullptr, g->nsel, Apsi, psi_k, sc.st));
     }
   }
   return TACAW_OK;
 }
 
-int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
-                  int32_t reduce, const int32_t* qsel, int64_t nsel, float* S_out, Scratch& sc);
-
 // Argument checks shared by tacaw_run and tacaw_submit.
 int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr, const float* pos,
               const int32_t* Z, int64_t n_atoms, int64_t n_frames, int32_t precision, int32_t reduce,
-              const float* S_out) {
+              const float* S_out, bool buffers) {
   TRY_RC(check_params(ctx, params));
   if (n_atoms < 0 || n_frames < 1 || pr.n_probes < 1) return set_err(ctx, TACAW_EINVAL, "bad sizes");
   if (n_frames > 65535 || pr.n_probes > 65535) return set_err(ctx, TACAW_EINVAL, "frames and probes must be <= 65535");
@@ -728,8 +785,8 @@ int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr,
   if (pr.psi0 && !is_device_ptr(pr.psi0)) return set_err(ctx, TACAW_EINVAL, "probe psi0 must be a device pointer");
   TRY_RC(check_spread_band(ctx, params));
   if (ctx->ffZ.empty()) return set_err(ctx, TACAW_EINVAL, "no form-factor table loaded");
-  if (!pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
-  if (!S_out || (!Z && n_atoms > 0)) return set_err(ctx, TACAW_EINVAL, "Z, S_out must not be NULL");
+  if (buffers && !pos && n_atoms > 0) return set_err(ctx, TACAW_EINVAL, "pos is NULL");
+  if (buffers && (!S_out || (!Z && n_atoms > 0))) return set_err(ctx, TACAW_EINVAL, "Z, S_out must not be NULL");
   if (reduce != TACAW_REDUCE_NONE && reduce != TACAW_REDUCE_DETECTOR) return set_err(ctx, TACAW_EINVAL, "bad reduce");
   if (precision < TACAW_DFT_FP32 || precision > TACAW_DFT_TF32) return set_err(ctx, TACAW_EINVAL, "bad precision");
   return TACAW_OK;
@@ -738,14 +795,16 @@ int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr,
 // Tiling of a run: frames per chunk and slices per block.  A chunk's scratch stays under
 // 2 GB; the slice block shrinks below S only when that is what lets one slice launch hold at
 // least kMinWaveRows wave rows (several waves of CTAs on every SM), so that the number of
-// waves per launch does not fall with the slice count or the grid size.
+// waves per launch does not fall with the slice count or the grid size.  P is the number of
+// probes propagated together (one probe block).
 constexpr int64_t kMinWaveRows = 65536;  // default of the "min_wave_rows" option
+constexpr size_t kChunkCap = (size_t)2 << 30;
 struct RunTiling {
   int64_t chunk;
   int sb;
 };
 RunTiling run_tiling(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t F) {
-  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp, cap = (size_t)2 << 30;
+  const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp, cap = kChunkCap;
   const int S = p.n_slices;
   const size_t per_slice = nq * 8 + plane * 8 * (g->npair + 3), wave = (size_t)P * plane * 16;
   const int64_t rows = ctx->min_wave_rows > 0 ? ctx->min_wave_rows : kMinWaveRows;
@@ -762,68 +821,153 @@ RunTiling run_tiling(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache
   return RunTiling{c, sb};
 }
 
+// Probe blocks of a run.  Every probe needs its exit-wave stack (F in-band points, compact)
+// and the time transform's operands until its block is transformed; probes are therefore
+// propagated and transformed in blocks of Pb, sized so that a run's scratch stays under the
+// context's "max_run_bytes" (default: half the serving budget, at most 64 GiB).  When there is
+// more than one block and the transmission functions of the whole trajectory fit a quarter of
+// that bound, they are built once and kept; otherwise every block rebuilds them.
+struct RunPlan {
+  int Pb = 1;         // probes per block
+  int nblocks = 1;
+  bool keep_t = false;
+  bool tf = false;    // compact transmission functions, inverse-transformed by the row pass
+  RunTiling rt{1, 1};
+};
+
+double spectrum_bytes_per_probe(const GeoCache* g, int64_t F, int32_t precision, int32_t reduce) {
+  const double nsel = (double)g->nsel;
+  double b = nsel * 16;  // mean
+  if (precision == TACAW_DFT_FP32) {
+    b += (double)F * nsel * 8;                                    // residual
+    if (reduce == TACAW_REDUCE_DETECTOR) b += (double)F * nsel * 4;  // compact S
+  } else {
+    const double esz = (precision == TACAW_DFT_TF32X3 || precision == TACAW_DFT_TF32) ? 4 : 2;
+    const double cpp = std::ceil(nsel / 256.0) * 256.0, kpad = std::ceil(2.0 * F / 64.0) * 64.0 + 32;
+    b += cpp * kpad * esz * 2;                                               // B_hi, B_lo
+    if (reduce == TACAW_REDUCE_DETECTOR) b += cpp / 256.0 * (double)F * 8;  // tile partial sums
+  }
+  return b;
+}
+
+uint64_t run_cap(const tacaw_ctx* ctx) {
+  if (ctx->max_run_bytes > 0) return (uint64_t)ctx->max_run_bytes;
+  return std::min<uint64_t>(ctx->budget / 2, (uint64_t)64 << 30);
+}
+
+RunPlan run_plan(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t F, int64_t A,
+                 int32_t precision, int32_t reduce) {
+  RunPlan pl;
+  const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
+  const double fixed = (double)F * A * 44 + (double)F * (S + 1) * 4 + (double)F * S * (p.ny / SPREAD_YB + 1) * 4;
+  const double per_probe = nq * 8 + plane * 8 + (double)F * g->nsel * 8 + spectrum_bytes_per_probe(g, F, precision,
+                                                                                                    reduce);
+  const double cap = (double)run_cap(ctx);
+  double room = cap - fixed - 2.0 * (double)kChunkCap;
+  int64_t pb = room > per_probe ? (int64_t)(room / per_probe) : 1;
+  if (ctx->max_probe_block > 0) pb = std::min<int64_t>(pb, ctx->max_probe_block);
+  pb = std::max<int64_t>(1, std::min<int64_t>(pb, P));
+  pl.nblocks = (int)((P + pb - 1) / pb);
+  pl.Pb = (int)((P + pl.nblocks - 1) / pl.nblocks);  // even blocks
+  pl.tf = use_compact_t(p, pl.Pb);
+  pl.keep_t = pl.nblocks > 1 && (double)F * S * (pl.tf ? plane : nq) * 8 <= 0.25 * cap;
+  pl.rt = run_tiling(ctx, p, g, pl.Pb, F);
+  if (pl.keep_t) {
+    // the kept t is laid out [F][S]: every chunk builds all its slices at once
+    pl.rt.sb = p.n_slices;
+    const size_t per_frame = (size_t)S * plane * 8 * (g->npair + 2) + (size_t)pl.Pb * plane * 16;
+    pl.rt.chunk = std::min<int64_t>(pl.rt.chunk, chunk_frames(F, per_frame, kChunkCap));
+  }
+  return pl;
+}
+
 // Device bytes a run allocates from the stream-ordered pool (tables cached in the context
 // are not counted), mirroring run_impl; used to admit serving requests.
 uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
                        int32_t reduce, GeoCache* g) {
+  const RunPlan pl = run_plan(ctx, p, g, P, F, A, precision, reduce);
   const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
-  const RunTiling rt = run_tiling(ctx, p, g, P, F);
-  const double chunk = (double)rt.chunk, sb = rt.sb;
+  const double chunk = (double)pl.rt.chunk, sb = pl.rt.sb, Pb = pl.Pb;
+  const double tsz = (pl.tf ? plane : nq) * 8;
   double b = 0;
   b += (double)F * A * (12 + 16 + 16) + (double)F * (S + 1) * 4 + A;  // positions, records (binned, row-sorted), slots
   b += (double)F * S * (p.ny / SPREAD_YB + 1) * 4;                      // row-block offsets
-  b += chunk * sb * plane * 8 * (g->npair + 2);                      // Bp, Ap, Bt
-  b += chunk * sb * nq * 8;                                           // t (or At)
-  b += chunk * (double)P * plane * 16;                                // Apsi, Bpsi
-  b += (double)P * nq * 16;                                           // probes
-  b += (double)P * F * nq * 8;                                        // exit waves
-  b += (double)P * g->nsel * 16;                                      // mean
-  const double ncols = (double)P * g->nsel;
-  if (precision == TACAW_DFT_FP32) b += (double)F * ncols * 8;
-  else {
-    const double esz = (precision == TACAW_DFT_TF32X3 || precision == TACAW_DFT_TF32) ? 4 : 2;
-    b += ncols * (2.0 * F + 64) * esz * 2;
-  }
-  b += reduce == TACAW_REDUCE_NONE ? (double)P * F * nq * 4 : (double)P * F * nq * 4 + (double)P * F * 4;
+  b += chunk * sb * plane * 8 * (g->npair + 2);                         // Bp, Ap, Bt
+  if (!pl.tf) b += chunk * sb * plane * 8;                              // At
+  b += pl.keep_t ? (double)F * S * tsz : chunk * sb * tsz;             // t
+  b += chunk * Pb * plane * 16;                                         // Apsi, Bpsi
+  b += Pb * (nq * 8 + plane * 8);                                       // probes (and their column pass)
+  b += Pb * (double)F * g->nsel * 8;                                    // compact exit waves
+  b += Pb * spectrum_bytes_per_probe(g, F, precision, reduce);
   return (uint64_t)(b * 1.05) + ((uint64_t)64 << 20);
 }
 
 // The whole path on device buffers, stream-ordered: positions d_pos [F][A][3] (device), Z
-// (host or device), S into d_S (device).  Scratch comes from the stream-ordered pool.
+// (host or device), S into d_S (device).  Scratch comes from the stream-ordered pool.  Probes
+// run in blocks (RunPlan): each block's waves are propagated through every frame, their
+// compact exit-wave stack is transformed, and the block's scratch is released before the next.
 int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const float* d_pos, const int32_t* Z,
              bool z_dev, int64_t A, int64_t F, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st) {
   GeoCache* g;
   TRY_RC(get_geo(ctx, p, &g));
   Scratch sc(st);
-  const int P = pr.n_probes;
+  const int P = pr.n_probes, S = p.n_slices;
   const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
+  const RunPlan pl = run_plan(ctx, p, g, P, F, A, precision, reduce);
+  const RunTiling rt = pl.rt;
+  const size_t tsz = pl.tf ? plane : nq;
   int8_t* slots;
   TRY_RC(make_slots(ctx, Z, A, z_dev, true, sc, &slots));
-  float2* psi0 = nullptr;
-  if (pr.psi0) psi0 = const_cast<float2*>(reinterpret_cast<const float2*>(pr.psi0));
-  else if (pr.alpha_mrad > 0.0) TRY_RC(build_probes(ctx, p, pr, sc, &psi0));
-  float2* psi_k;
-  CK(sc.get(&psi_k, (size_t)P * F * nq));
-  CK(cudaMemsetAsync(psi_k, 0, sizeof(float2) * P * F * nq, st));
-  const RunTiling rt = run_tiling(ctx, p, g, P, F);
-  float2 *t, *Apsi, *Bpsi;
-  CK(sc.get(&t, (size_t)rt.chunk * rt.sb * nq));
-  CK(sc.get(&Apsi, (size_t)rt.chunk * P * plane));
-  CK(sc.get(&Bpsi, (size_t)rt.chunk * P * plane));
-  const bool tf = use_compact_t(p, P);
+  Binned bn;
+  TRY_RC(bin_frames(ctx, p, d_pos, slots, A, F, sc, &bn));
+  float2 *Bp, *Ap, *t;
+  CK(sc.get(&Bp, (size_t)rt.chunk * rt.sb * g->npair * plane));
+  CK(sc.get(&Ap, (size_t)rt.chunk * rt.sb * plane));
+  CK(sc.get(&t, pl.keep_t ? (size_t)F * S * tsz : (size_t)rt.chunk * rt.sb * tsz));
   TransBufs tb;
-  TRY_RC(trans_bufs(ctx, p, g, rt.chunk * rt.sb, tf, sc, &tb));
-  TRY_RC(potential_chunks(ctx, p, g, d_pos, slots, A, F, rt.chunk, rt.sb, sc,
-                          [&](int64_t f0, int nfc, int s0, int sbc, float2* Ap) {
-    {
-      NvtxRange r("transmission");
-      TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * sbc, t, sc, tb, tf));
+  TRY_RC(trans_bufs(ctx, p, g, rt.chunk * rt.sb, pl.tf, sc, &tb));
+  const SpecIO io{g->nsel, nullptr, g->nsel, (int64_t)nq, g->qsel};
+  for (int blk = 0; blk < pl.nblocks; ++blk) {
+    const int p0 = blk * pl.Pb, Pbc = std::min(pl.Pb, P - p0);
+    if (Pbc <= 0) break;
+    Scratch bsc(st);  // released on the stream at the end of the block
+    float2* psi0 = nullptr;
+    if (pr.psi0) {
+      psi0 = const_cast<float2*>(reinterpret_cast<const float2*>(pr.psi0)) + (size_t)p0 * nq;
+    } else if (pr.alpha_mrad > 0.0) {
+      tacaw_probe sub = pr;
+      sub.n_probes = Pbc;
+      sub.xy = pr.xy ? pr.xy + 2 * (size_t)p0 : nullptr;
+      TRY_RC(build_probes(ctx, p, sub, bsc, &psi0));
     }
-    NvtxRange r("multislice");
-    return slices(ctx, p, g, t, nfc, s0, sbc, P, psi0, F, f0, psi_k, sc, Apsi, Bpsi, tf);
-  }));
-  NvtxRange r("time_dft");
-  return spectrum_impl(ctx, psi_k, P, F, (int64_t)nq, precision, reduce, g->qsel, g->nsel, d_S, sc);
+    float2 *psi_k, *Apsi, *Bpsi;
+    CK(bsc.get(&psi_k, (size_t)Pbc * F * g->nsel));
+    CK(bsc.get(&Apsi, (size_t)rt.chunk * Pbc * plane));
+    CK(bsc.get(&Bpsi, (size_t)rt.chunk * Pbc * plane));
+    const bool build_t = blk == 0 || !pl.keep_t;
+    for (int64_t f0 = 0; f0 < F; f0 += rt.chunk) {
+      const int nfc = (int)std::min<int64_t>(rt.chunk, F - f0);
+      for (int s0 = 0; s0 < S; s0 += rt.sb) {
+        const int sbc = std::min(rt.sb, S - s0);
+        float2* tblk = pl.keep_t ? t + (size_t)f0 * S * tsz : t;
+        if (build_t) {
+          TRY_RC(potential_block(ctx, p, g, bn, A, f0, nfc, s0, sbc, Bp, Ap, st));
+          NvtxRange r("transmission");
+          TRY_RC(transmission_from(ctx, p, g, Ap, nullptr, nfc * sbc, tblk, sc, tb, pl.tf));
+        }
+        NvtxRange r("multislice");
+        if (pl.keep_t)
+          TRY_RC(slices(ctx, p, g, tblk, S, 0, nfc, s0, sbc, Pbc, psi0, F, f0, psi_k, true, sc, Apsi, Bpsi, pl.tf));
+        else
+          TRY_RC(slices(ctx, p, g, tblk, sbc, s0, nfc, s0, sbc, Pbc, psi0, F, f0, psi_k, true, sc, Apsi, Bpsi,
+                        pl.tf));
+      }
+    }
+    NvtxRange r("time_dft");
+    float* out = d_S + (reduce == TACAW_REDUCE_NONE ? (size_t)p0 * F * nq : (size_t)p0 * F);
+    TRY_RC(spectrum_impl(ctx, psi_k, Pbc, F, io, precision, reduce, out, bsc));
+  }
+  return TACAW_OK;
 }
 
 }  // namespace tacaw
@@ -940,7 +1084,7 @@ int tacaw_propagate(tacaw_ctx* ctx, const tacaw_params* params, const float* V, 
   for (int64_t f0 = 0; f0 < nf; f0 += chunk) {
     const int nfc = (int)std::min<int64_t>(chunk, nf - f0);
     TRY_RC(transmission_from(ctx, p, g, nullptr, V + (size_t)f0 * S * nq, nfc * S, t, sc, tb, tf));
-    TRY_RC(slices(ctx, p, g, t, nfc, 0, S, P, psi0, nf, f0, psi_k, sc, Apsi, Bpsi, tf));
+    TRY_RC(slices(ctx, p, g, t, S, 0, nfc, 0, S, P, psi0, nf, f0, psi_k, false, sc, Apsi, Bpsi, tf));
   }
   return TACAW_OK;
 }
@@ -956,8 +1100,8 @@ int tacaw_spectrum(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t F, int
   if (q_sel && (n_sel < 1 || n_sel > nq)) return set_err(ctx, TACAW_EINVAL, "n_sel must be in [1, nq]");
   CK(cudaSetDevice(ctx->device));
   Scratch sc((cudaStream_t)stream);
-  return spectrum_impl(ctx, reinterpret_cast<const float2*>(psi_k), P, F, nq, precision, reduce, q_sel,
-                       q_sel ? n_sel : nq, S_out, sc);
+  const SpecIO io{nq, q_sel, q_sel ? n_sel : nq, nq, q_sel};
+  return spectrum_impl(ctx, reinterpret_cast<const float2*>(psi_k), P, F, io, precision, reduce, S_out, sc);
 }
 
 int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, const int32_t* Z, int64_t n_atoms,
@@ -967,7 +1111,7 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   tacaw::NvtxRange nvtx("tacaw_run");
   tacaw_probe pr = probe ? *probe : default_probe();
-  TRY_RC(check_run(ctx, params, pr, pos, Z, n_atoms, n_frames, precision, reduce, S_out));
+  TRY_RC(check_run(ctx, params, pr, pos, Z, n_atoms, n_frames, precision, reduce, S_out, true));
   const tacaw_params& p = *params;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1012,6 +1156,16 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (std::strcmp(name, "max_slice_block") == 0) {
     if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_slice_block must be >= 0");
     ctx->max_slice_block = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "max_run_bytes") == 0) {
+    if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_run_bytes must be >= 0");
+    ctx->max_run_bytes = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "max_probe_block") == 0) {
+    if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_probe_block must be >= 0");
+    ctx->max_probe_block = value;
     return TACAW_OK;
   }
   return set_err(ctx, TACAW_EINVAL, "unknown option '%s'", name);
@@ -1104,40 +1258,44 @@ int tacaw_profile_end(tacaw_ctx* ctx, char* names, double* ms, int64_t* launches
 
 namespace tacaw {
 
-int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, int64_t nq, int32_t precision,
-                  int32_t reduce, const int32_t* qsel, int64_t nsel, float* S_out, Scratch& sc) {
+int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, const SpecIO& io, int32_t precision,
+                  int32_t reduce, float* S_out, Scratch& sc) {
   if (reduce != TACAW_REDUCE_NONE && reduce != TACAW_REDUCE_DETECTOR) return set_err(ctx, TACAW_EINVAL, "bad reduce");
   if (precision < TACAW_DFT_FP32 || precision > TACAW_DFT_TF32) return set_err(ctx, TACAW_EINVAL, "bad precision");
   cudaStream_t st = sc.st;
+  const int64_t nsel = io.nsel;
   double2* mean;
   CK(sc.get(&mean, (size_t)P * nsel));
   const double pfq = (double)P * F * nsel;
   {
     ProfScope ps(ctx, "mean_f64", st, pfq * 8 + (double)P * nsel * 16, pfq * 2);
-    CK(launch_mean_f64(psi_k, P, F, nq, qsel, nsel, mean, st));
+    CK(launch_mean_f64(psi_k, P, F, io.in_nq, io.in_qsel, nsel, mean, st));
   }
-  float* S = S_out;
-  if (reduce == TACAW_REDUCE_DETECTOR) CK(sc.get(&S, (size_t)P * F * nq));
-  if (reduce == TACAW_REDUCE_NONE && qsel && nsel < nq) CK(cudaMemsetAsync(S, 0, sizeof(float) * P * F * nq, st));
+  const bool det = reduce == TACAW_REDUCE_DETECTOR;
+  if (!det && io.out_qsel && nsel < io.out_nq) CK(cudaMemsetAsync(S_out, 0, sizeof(float) * P * F * io.out_nq, st));
   if (precision == TACAW_DFT_FP32) {
     float2* r;
     CK(sc.get(&r, (size_t)P * F * nsel));
     {
       ProfScope ps(ctx, "residual_f32", st, pfq * 16, pfq * 2);
-      CK(launch_residual_f32(psi_k, mean, P, F, nq, qsel, nsel, r, st));
+      CK(launch_residual_f32(psi_k, mean, P, F, io.in_nq, io.in_qsel, nsel, r, st));
     }
     float2* twF;
     TRY_RC(get_time_tw(ctx, F, &twF));
-    ProfScope ps(ctx, "dft_fp32", st, pfq * 12, pfq * 8.0 * F);
-    CK(launch_dft_fp32(r, twF, P, F, nsel, nq, qsel, S, st));
-  } else {
-    TRY_RC(spectrum_tc(ctx, psi_k, mean, P, F, nq, precision, qsel, nsel, S, sc));
+    // the detector sum reads a compact S [P][F][nsel]
+    float* S = S_out;
+    if (det) CK(sc.get(&S, (size_t)P * F * nsel));
+    {
+      ProfScope ps(ctx, "dft_fp32", st, pfq * 12, pfq * 8.0 * F);
+      CK(launch_dft_fp32(r, twF, P, F, nsel, det ? nsel : io.out_nq, det ? nullptr : io.out_qsel, S, st));
+    }
+    if (det) {
+      ProfScope ps(ctx, "detector_reduce", st, pfq * 4, pfq);
+      CK(launch_detector_reduce(S, P, F, nsel, nullptr, nsel, S_out, st));
+    }
+    return TACAW_OK;
   }
-  if (reduce == TACAW_REDUCE_DETECTOR) {
-    ProfScope ps(ctx, "detector_reduce", st, pfq * 4, pfq);
-    CK(launch_detector_reduce(S, P, F, nq, qsel, nsel, S_out, st));
-  }
-  return TACAW_OK;
+  return spectrum_tc(ctx, psi_k, mean, P, F, io, precision, reduce, S_out, sc);
 }
 
 }  // namespace tacaw

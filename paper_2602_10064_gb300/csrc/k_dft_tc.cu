@@ -17,7 +17,12 @@
 // K steps (the frames of a long trajectory) the error would grow linearly; instead the MMAs
 // of one chunk of TC_KC K blocks accumulate in TMEM (two 256-column buffers, alternating),
 // and after every chunk warps 2..9 add the chunk's partial sums into FP32 registers on the
-// CUDA cores (round to nearest).  At the end those warps form S = D[2w]^2 + D[2w+1]^2.
+// CUDA cores (round to nearest).  At the end those warps form S = D[2w]^2 + D[2w+1]^2 and either
+// store it (full S) or, for the detector-summed spectrum image, add it up over the tile's
+// columns in FP64 and store one partial sum per (tile, w); a second kernel adds the partial sums
+// of each probe in a fixed order, so S is never written and the result is deterministic.
+// The columns of B are laid out per probe, cpp (a multiple of the tile width) per probe, so
+// every tile belongs to one probe; columns j >= nsel of a probe are zero.
 // Every wait is bounded (%globaltimer); on expiry the kernel sets the context's status word
 // and leaves without hanging.
 #include <cuda.h>
@@ -39,7 +44,8 @@ constexpr int TC_EPI_COLS = TC_BN / 2;  // accumulator columns per epilogue thre
 constexpr int TC_ROW_BYTES = 128;  // one swizzle span of K per tile row
 constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES, TC_B_BYTES = TC_BN * TC_ROW_BYTES;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/ +
+                        TC_BM * 8 /*detector partial sums of the two column halves*/;
 constexpr int TC_TMEM_COLS = 2 * TC_BN;  // two accumulator buffers
 constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 
@@ -159,13 +165,15 @@ template <bool TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_dft_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
              const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int mtiles,
-             int nphase, int nkb, int64_t F, int64_t ncols, int64_t nsel, int64_t nq, const int32_t* __restrict__ qsel,
-             float* __restrict__ S, int* __restrict__ status) {
+             int nphase, int nkb, int64_t F, int64_t cpp, int64_t nsel, int64_t out_nq,
+             const int32_t* __restrict__ out_qsel, float* __restrict__ S, double* __restrict__ part,
+             int* __restrict__ status) {
   extern __shared__ uint8_t smraw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
   // bars: full[S], empty[S], acc_full[2], acc_empty[2], drain; then the TMEM base address
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  double* red = reinterpret_cast<double*>(smem + TC_STAGES * TC_STAGE_BYTES + 256);  // [2][TC_BM / 2]
   const uint32_t drain = smem_u32(bars + 2 * TC_STAGES + 4);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES);
   const uint32_t accf0 = smem_u32(bars + 2 * TC_STAGES), acce0 = smem_u32(bars + 2 * TC_STAGES + 2);
@@ -273,21 +281,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
     }
-    if (ok) {
-      // rows m0 + 32 quarter + lane: even lanes hold Re, odd lanes Im of psi~(w)
-      const int m = m0 + 32 * quarter + lane;
-      const int64_t w = m >> 1;
-      const bool writer = ((lane & 1) == 0) && w < F;
+    // rows m0 + 32 quarter + lane: even lanes hold Re, odd lanes Im of psi~(w); the tile's
+    // columns all belong to probe p (cpp is a multiple of TC_BN)
+    const int m = m0 + 32 * quarter + lane;
+    const int64_t w = m >> 1;
+    const bool writer = ((lane & 1) == 0) && w < F;
+    const int64_t p = n0 / cpp, j0 = n0 - p * cpp + half * TC_EPI_COLS;
+    if (!part) {
+      if (ok) {
+#pragma unroll
+        for (int i = 0; i < TC_EPI_COLS; ++i) {
+          const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
+          const float sv = acc[i] * acc[i] + o * o;
+          const int64_t j = j0 + i;
+          if (writer && j < nsel) {
+            const int64_t q = out_qsel ? out_qsel[j] : j;
+            S[((size_t)p * F + w) * out_nq + q] = sv;
+          }
+        }
+      }
+    } else {
+      // detector sum: |psi~|^2 rounded to float as a stored S would be, summed in FP64 over
+      // this thread's columns, then over the two column halves in a fixed order
+      double dsum = 0.0;
 #pragma unroll
       for (int i = 0; i < TC_EPI_COLS; ++i) {
         const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
         const float sv = acc[i] * acc[i] + o * o;
-        const int64_t J = n0 + half * TC_EPI_COLS + i;
-        if (writer && J < ncols) {
-          const int64_t p = J / nsel, j = J - p * nsel;
-          const int64_t q = qsel ? qsel[j] : j;
-          S[((size_t)p * F + w) * nq + q] = sv;
-        }
+        if (j0 + i < nsel) dsum += (double)sv;
+      }
+      if ((lane & 1) == 0) red[half * (TC_BM / 2) + ((32 * quarter + lane) >> 1)] = dsum;
+      // every epilogue warp arrives here, also after a timed-out wait
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
+      if (ok && half == 0 && writer) {
+        const int r = (32 * quarter + lane) >> 1;
+        part[(size_t)(n0 / TC_BN) * F + w] = red[r] + red[TC_BM / 2 + r];
       }
     }
   }
@@ -311,20 +339,21 @@ __device__ __forceinline__ float to_tf32(float x) {
 template <bool TF32>
 __global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict__ psi, const double2* __restrict__ mean,
                                                         int64_t F, int64_t nq, const int32_t* __restrict__ qsel,
-                                                        int64_t nsel, int64_t P, int kpad2, void* __restrict__ Bhi,
-                                                        void* __restrict__ Blo) {
+                                                        int64_t nsel, int64_t cpp, int64_t P, int kpad2,
+                                                        void* __restrict__ Bhi, void* __restrict__ Blo) {
   __shared__ float2 hs[32][33], ls[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t J0 = (int64_t)blockIdx.x * 32;
   const int64_t n0 = (int64_t)blockIdx.y * 32;
-  const int64_t ncols = P * nsel;
-  // phase 1: coalesced along j
+  const int64_t ncols = P * cpp;
+  // phase 1: coalesced along j; columns j >= nsel of a probe (padding) are zero
   const int64_t J = J0 + tx;
   int64_t p = 0, j = 0, q = 0;
   float mxh = 0.f, mxl = 0.f, myh = 0.f, myl = 0.f;
-  if (J < ncols) {
-    p = J / nsel;
-    j = J - p * nsel;
+  const bool live = J < ncols && J - (J / cpp) * cpp < nsel;
+  if (live) {
+    p = J / cpp;
+    j = J - p * cpp;
     q = qsel ? qsel[j] : j;
     const double2 mu = mean[(size_t)p * nsel + j];
     split_double(mu.x, mxh, mxl);
@@ -333,7 +362,7 @@ __global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict
   for (int r = ty; r < 32; r += 8) {
     const int64_t n = n0 + r;
     float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
-    if (J < ncols && n < F) {
+    if (live && n < F) {
       const float2 v = psi[((size_t)p * F + n) * nq + q];
       float rx, ex, ry, ey;
       pair_sub(v.x, mxh, mxl, rx, ex);
@@ -370,6 +399,18 @@ __global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict
       reinterpret_cast<__nv_bfloat162*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = ll;
     }
   }
+}
+
+// Spectrum image from the detector partial sums: SI[p][w] = sum over the tpp tiles of probe p of
+// part[tile][w], in FP64 and in tile order, rounded to float.
+__global__ void k_detector_tiles(const double* __restrict__ part, int64_t P, int64_t F, int64_t tpp,
+                                 float* __restrict__ SI) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (w >= F || p >= P) return;
+  const double* col = part + (size_t)p * tpp * F + w;
+  double s = 0.0;
+  for (int64_t t = 0; t < tpp; ++t) s += col[(size_t)t * F];
+  SI[(size_t)p * F + w] = (float)s;
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing ever arrives on,
@@ -496,14 +537,16 @@ int get_dft_operands(tacaw_ctx* ctx, int64_t F, bool tf32, int64_t kpad, void** 
   return TACAW_OK;
 }
 
-int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, int64_t nq,
-                int32_t precision, const int32_t* qsel, int64_t nsel, float* S, Scratch& sc) {
+int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, const SpecIO& io,
+                int32_t precision, int32_t reduce, float* S, Scratch& sc) {
   const bool tf32 = precision == TACAW_DFT_TF32X3 || precision == TACAW_DFT_TF32;
   const int nphase = (precision == TACAW_DFT_BF16X3 || precision == TACAW_DFT_TF32X3) ? 3 : 1;
   const int esz = tf32 ? 4 : 2;
   const int kblk = TC_ROW_BYTES / esz;                 // K elements per block
   const int64_t kpad = ((2 * F + kblk - 1) / kblk) * kblk;
-  const int64_t ncols = P * nsel;
+  const int64_t nsel = io.nsel;
+  const int64_t cpp = (nsel + TC_BN - 1) / TC_BN * TC_BN;  // columns per probe, whole tiles
+  const int64_t ncols = P * cpp;
   if (ncols > ((int64_t)1 << 31) - 1 || kpad > (1 << 24)) return set_err(ctx, TACAW_EINVAL, "spectrum too large");
   if (!encode_fn()) return set_err(ctx, TACAW_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   void *Ahi, *Alo;
@@ -519,9 +562,11 @@ int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_
     const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((kpad / 2 + 31) / 32));
     if (grid.y > 65535) return set_err(ctx, TACAW_EINVAL, "too many frames");
     if (tf32)
-      k_residual_split<true><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, nq, qsel, nsel, P, (int)kpad, Bhi, Blo);
+      k_residual_split<true><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, io.in_nq, io.in_qsel, nsel, cpp, P, (int)kpad,
+                                                      Bhi, Blo);
     else
-      k_residual_split<false><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, nq, qsel, nsel, P, (int)kpad, Bhi, Blo);
+      k_residual_split<false><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, io.in_nq, io.in_qsel, nsel, cpp, P,
+                                                       (int)kpad, Bhi, Blo);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_residual_split");
   }
@@ -530,24 +575,41 @@ int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_
       !make_map(&mBhi, Bhi, tf32, ncols, kpad, TC_BN) || !make_map(&mBlo, Blo, tf32, ncols, kpad, TC_BN))
     return set_err(ctx, TACAW_ECUDA, "tensor map encoding failed");
   const int mtiles = (int)((2 * F + TC_BM - 1) / TC_BM);
-  const int64_t ntiles = (ncols + TC_BN - 1) / TC_BN;
+  const int64_t ntiles = ncols / TC_BN;
   const int64_t tiles = (int64_t)mtiles * ntiles;
+  if (tiles > ((int64_t)1 << 31) - 1) return set_err(ctx, TACAW_EINVAL, "spectrum too large");
   const int nkb = (int)(kpad / kblk);
+  double* part = nullptr;
+  const bool det = reduce == TACAW_REDUCE_DETECTOR;
+  if (det) {
+    e = sc.get(&part, (size_t)ntiles * F);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "detector partial sums");
+  }
   e = tf32 ? cudaFuncSetAttribute(k_dft_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
            : cudaFuncSetAttribute(k_dft_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaFuncSetAttribute");
   {
-    const double flops = 8.0 * F * F * (double)ncols * nphase;
+    const double flops = 8.0 * F * F * (double)P * nsel * nphase;
+    const double out_bytes = det ? (double)ntiles * F * 8 : (double)P * nsel * F * 4;
     ProfScope ps(ctx, tf32 ? "dft_tc_tf32" : "dft_tc_bf16", sc.st,
-                 (double)ncols * kpad * esz * (nphase > 1 ? 2 : 1) + (double)ncols * F * 4, flops);
+                 (double)ncols * kpad * esz * (nphase > 1 ? 2 : 1) + out_bytes, flops);
     if (tf32)
       k_dft_tc<true><<<(unsigned)tiles, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, nphase, nkb, F,
-                                                                     ncols, nsel, nq, qsel, S, ctx->d_status);
+                                                                     cpp, nsel, io.out_nq, io.out_qsel, S, part,
+                                                                     ctx->d_status);
     else
       k_dft_tc<false><<<(unsigned)tiles, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, nphase, nkb,
-                                                                      F, ncols, nsel, nq, qsel, S, ctx->d_status);
+                                                                      F, cpp, nsel, io.out_nq, io.out_qsel, S, part,
+                                                                      ctx->d_status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_dft_tc");
+  }
+  if (det) {
+    ProfScope ps(ctx, "detector_tiles", sc.st, (double)ntiles * F * 8 + (double)P * F * 4, (double)ntiles * F);
+    if (P > 65535) return set_err(ctx, TACAW_EINVAL, "too many probes");
+    k_detector_tiles<<<dim3((unsigned)((F + 127) / 128), (unsigned)P), 128, 0, sc.st>>>(part, P, F, cpp / TC_BN, S);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "k_detector_tiles");
   }
   return TACAW_OK;
 }

@@ -779,7 +779,7 @@ template <int NY, bool LAST>
 __global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL, NY, SliceColCfg<NY>>())
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
-                float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
+                const int2* __restrict__ disc, int64_t nsel, float2* __restrict__ Apsi, float2* __restrict__ psi_k) {
   using CC = SliceColCfg<NY>;
   constexpr int E = CC::E, T = CC::T, C = CC::C;
   constexpr int PL = Tuned<K_SLICE_COL, NY>::PLAN;
@@ -806,10 +806,26 @@ __global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL,
   if (LAST) {
     if (cc < b.W) {
       const int p = w / nfc, fl = w - p * nfc;
-      const int x = band_col_x(b, geo.nx, cc);
-      float2* dst = psi_k + (((size_t)p * F_total + f0 + fl) * NY) * geo.nx + x;
+      if (disc) {
+        // compact exit wave: the in-band points of the disc only, in ascending q = y nx + x;
+        // row y holds disc[y].y points from disc[y].x on, with x in [0, a] then [nx - a, nx)
+        float2* dst = psi_k + ((size_t)p * F_total + f0 + fl) * nsel;
 #pragma unroll
-      for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * geo.nx] = v[e];
+        for (int e = 0; e < E; ++e) {
+          const int row = t + T * e, n = fftfreq_index(row, NY);
+          if (abs(n) <= nb) {
+            const int2 d = disc[row];
+            const int a = (d.y - 1) >> 1;
+            const int j = d.y == geo.nx ? cc : (cc <= a ? cc : cc - b.W + 2 * a + 1);
+            dst[d.x + j] = v[e];
+          }
+        }
+      } else {
+        const int x = band_col_x(b, geo.nx, cc);
+        float2* dst = psi_k + (((size_t)p * F_total + f0 + fl) * NY) * geo.nx + x;
+#pragma unroll
+        for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * geo.nx] = v[e];
+      }
     }
     return;
   }
@@ -1030,7 +1046,7 @@ cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, 
 template <int NY>
 static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
                                const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
-                               float2* Apsi, float2* psi_k, cudaStream_t st) {
+                               const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st) {
   const int nw = P * nfc;
   using CC = SliceColCfg<NY>;
   const dim3 grid = batch_grid(b.Wp / CC::C, nw);
@@ -1038,15 +1054,18 @@ static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const floa
   cudaError_t e = last ? prep(k_slice_col<NY, true>, SM) : prep(k_slice_col<NY, false>, SM);
   if (e != cudaSuccess) return e;
   if (last)
-    k_slice_col<NY, true><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, Apsi, psi_k);
+    k_slice_col<NY, true><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, disc, nsel, Apsi,
+                                                psi_k);
   else
-    k_slice_col<NY, false><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, Apsi, psi_k);
+    k_slice_col<NY, false><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, disc, nsel, Apsi,
+                                                 psi_k);
   return cudaGetLastError();
 }
 cudaError_t launch_slice_col(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
                              const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
-                             float2* Apsi, float2* psi_k, cudaStream_t st) {
-  TACAW_DISPATCH(g.ny, slice_col_n, g, b, last, Bpsi, px, py, scale, P, nfc, F_total, f0, Apsi, psi_k, st);
+                             const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, slice_col_n, g, b, last, Bpsi, px, py, scale, P, nfc, F_total, f0, disc, nsel, Apsi, psi_k,
+                 st);
 }
 
 cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot, const double* coef_slots,

@@ -262,7 +262,7 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
       pr.n_probes = 1;
     }
     int rc = check_run(ctx, &req->params, pr, req->pos, req->Z, req->n_atoms, req->n_frames, req->precision,
-                       req->reduce, req->S_out);
+                       req->reduce, req->S_out, true);
     if (rc != TACAW_OK) return rc;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
@@ -345,6 +345,29 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
     *ticket = j->ticket;
   }
   sv->cv.notify_all();
+  return TACAW_OK;
+}
+
+int tacaw_request_footprint(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* bytes) {
+  if (!ctx || !req || !bytes) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  tacaw_probe pr = req->probe;
+  if (pr.n_probes == 0) {
+    pr = tacaw_probe{};
+    pr.n_probes = 1;
+  }
+  int rc = check_run(ctx, &req->params, pr, req->pos, req->Z, req->n_atoms, req->n_frames, req->precision,
+                     req->reduce, req->S_out, false);
+  if (rc != TACAW_OK) return rc;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  GeoCache* g;
+  rc = get_geo(ctx, req->params, &g);
+  if (rc != TACAW_OK) return rc;
+  *bytes = run_footprint(ctx, req->params, pr.n_probes, req->n_frames, req->n_atoms, req->precision, req->reduce, g);
+  if (*bytes > ctx->budget)
+    return set_err(ctx, TACAW_ETOOBIG, "request needs %llu bytes, the budget is %llu", (unsigned long long)*bytes,
+                   (unsigned long long)ctx->budget);
   return TACAW_OK;
 }
 

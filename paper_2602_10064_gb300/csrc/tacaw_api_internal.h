@@ -40,6 +40,7 @@ struct GeoCache {
   double* coef_slots = nullptr;
   int32_t* qsel = nullptr;  // in-band q indices, ascending
   int64_t nsel = 0;
+  int2* disc = nullptr;     // [ny]: (first index in qsel, count) of each grid row's in-band points
   int npair = 0, nslot = 0;
   uint64_t ff_version = 0;
 };
@@ -76,6 +77,8 @@ struct tacaw_ctx {
   int64_t max_chunk_frames = 0;  // option: cap on frames per chunk (0 = automatic)
   int64_t max_slice_block = 0;   // option: cap on slices per block of a run (0 = automatic)
   int64_t min_wave_rows = 0;     // option: wave rows a slice launch should hold (0 = default)
+  int64_t max_run_bytes = 0;     // option: scratch bound of one run (0 = automatic)
+  int64_t max_probe_block = 0;   // option: cap on the probes propagated and transformed together
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };
@@ -112,17 +115,36 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// Where the time transform reads its input and writes its output.  Column j < nsel of the
+// transform reads psi[p][n][in_qsel ? in_qsel[j] : j] (row stride in_nq) and, for a full S,
+// writes S[p][m][out_qsel ? out_qsel[j] : j] (row stride out_nq).  The run path reads a compact
+// exit stack (in_nq = nsel, no in_qsel) and scatters into the full grid (out_qsel = the in-band
+// q list); tacaw_spectrum uses the caller's q_sel on both sides.
+struct SpecIO {
+  int64_t in_nq;
+  const int32_t* in_qsel;
+  int64_t nsel;
+  int64_t out_nq;
+  const int32_t* out_qsel;
+};
+
 int set_err(tacaw_ctx* c, int code, const char* fmt, ...);
 int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where);
 int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out);
 // tensor-core time transform (k_dft_tc.cu)
-int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, int64_t nq,
-                int32_t precision, const int32_t* qsel, int64_t nsel, float* S, Scratch& sc);
+// S: the full S (TACAW_REDUCE_NONE, written at the SpecIO output positions only) or the
+// spectrum image SI[P][F] (TACAW_REDUCE_DETECTOR: the sum over the nsel columns, fused into the
+// tensor-core epilogue).
+int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, const SpecIO& io,
+                int32_t precision, int32_t reduce, float* S, Scratch& sc);
+// The whole time transform (mean, residual, DFT, |.|^2, optional detector sum) on P probes.
+int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, const SpecIO& io, int32_t precision,
+                  int32_t reduce, float* S_out, Scratch& sc);
 // whole-path pieces (api.cu)
 int get_geo(tacaw_ctx* ctx, const tacaw_params& p, GeoCache** out);
 int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr, const float* pos,
               const int32_t* Z, int64_t n_atoms, int64_t n_frames, int32_t precision, int32_t reduce,
-              const float* S_out);
+              const float* S_out, bool buffers);
 uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
                        int32_t reduce, GeoCache* g);
 int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const float* d_pos, const int32_t* Z,

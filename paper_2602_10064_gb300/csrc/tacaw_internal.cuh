@@ -130,10 +130,13 @@ cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, in
 cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                              const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
                              float2* Bpsi, cudaStream_t st);
-// last = 0: Apsi = IFFT_y(P M scale FFT_y(Bpsi)); last = 1: psi_k[p][f0 + fl] = P M scale FFT_y(Bpsi).
+// last = 0: Apsi = IFFT_y(P M scale FFT_y(Bpsi)); last = 1: psi_k[p][f0 + fl] = P M scale FFT_y(Bpsi),
+// as the full [ny][nx] grid (disc = NULL; out-of-band points are not written) or, with disc, as
+// the nsel in-band points of the disc in ascending q: row y's points start at disc[y].x and
+// number disc[y].y.
 cudaError_t launch_slice_col(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
                              const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
-                             float2* Apsi, float2* psi_k, cudaStream_t st);
+                             const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st);
 // mtab[pair][ny][Wp] = C M(k) (f_2p(|k|) - i f_2p+1(|k|)) / (Phi_x Phi_y), FP64 evaluation.
 cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot, const double* coef_slots,
                               const double* phix, const double* phiy, double Lx, double Ly, double pref,

@@ -61,9 +61,11 @@ def test_sampling_relations_minimal_example():
         if line:
             k, v = line.split("=")
             vals[k.strip()] = float(v)
-    L = 20 * 5.431
-    dk, kmax, df, fmax = T.sampling(L, 0.1, 200, 10.0)
-    assert abs(L - vals["L_A"]) < 0.05
+    # the minimal example's cell (20 x 5.431 A, the paper's 108.6 A) at 0.1 A sampling: 1086 points
+    L = vals["L_A"]
+    assert abs(20 * 5.431 - L) < 0.05
+    p = T.make_params(1086, 1086, 54, (L, L, 27.155), dt_fs=10.0)
+    dk, kmax, df, fmax = T.sampling(p, 200)
     assert abs(dk - vals["dk_inv_A"]) < 0.0005
     assert abs(kmax - vals["kmax_inv_A"]) < 1e-12
     assert abs(df - vals["df_THz"]) < 1e-12
@@ -71,6 +73,12 @@ def test_sampling_relations_minimal_example():
     f = T.frequency_axis_thz(200, 10.0)
     assert abs(f[1] - 0.5) < 1e-12 and abs(f[100] + 50.0) < 1e-12
     assert np.allclose(T.k_axis(8, 4.0), np.fft.fftfreq(8, 0.5))
+    kx, ky, f2, smp = T.tacaw_axes(T.make_params(6, 4, 1, (3.0, 2.0, 1.0), dt_fs=2.0), 5)
+    assert np.allclose(kx, np.fft.fftfreq(6, 0.5)) and np.allclose(ky, np.fft.fftfreq(4, 0.5))
+    assert np.allclose(f2, np.fft.fftfreq(5, 2e-3))
+    assert np.allclose(smp, [1 / 3.0, 1 / 2.0, 1.0, 1.0, 100.0, 250.0])
+    with pytest.raises(T.TacawError):
+        T.tacaw_axes(T.make_params(6, 4, 1, (3.0, 2.0, 1.0), dt_fs=0.0), 5)
 
 
 def test_params_struct_layout():
