@@ -194,6 +194,35 @@ int tacaw_dispersion(tacaw_ctx* ctx, const float* S, int64_t P, int64_t F, int32
  * acc: DEVICE float64 [n]. */
 int tacaw_accumulate(tacaw_ctx* ctx, const float* S, int64_t n, double weight, double* acc, void* stream);
 
+/* ---- one trajectory split by frames across processes --------------------------------------- */
+
+/* In-band q points of a geometry: the q = y nx + x inside the 2/3-disc band limit (all q
+ * without one), ascending, that tacaw_run transforms.  *n_out receives their count; q_out
+ * (HOST int32, may be NULL) receives the list. */
+int tacaw_band_points(tacaw_ctx* ctx, const tacaw_params* params, int32_t* q_out, int64_t* n_out);
+
+/* Partial time transform of the frames [f0, f0 + nf) of an F-frame trajectory (Supplement,
+ * "Sampling Considerations": frames are independent until the time transform), for a
+ * trajectory split by frames across processes:
+ *   psi_tilde[p][m][j] = sum_{n < nf} exp(-2 pi i m (f0 + n) / F) (psi[p][n][q_j] - psi_ref[p][q_j]).
+ * Subtracting a time-independent reference instead of the frame mean (Methods, "Workflow
+ * Architecture") changes the transform only at m = 0, so the sum of the partial transforms of
+ * all processes (one all-reduce) gives every m != 0 bin; every process can use the exit wave
+ * of the trajectory's first frame as psi_ref without communication.  FP32 arithmetic.
+ * psi_k: DEVICE c64 [P][nf][nq]; psi_ref: DEVICE c64 [P][nq]; q_sel: DEVICE int32 [n_sel]
+ * (NULL: all nq); psi_tilde: DEVICE c64 [P][F][n_sel], overwritten.  EINVAL for f0 < 0,
+ * f0 + nf > F, sizes below 1, P or nf above 65535. */
+int tacaw_spectrum_partial(tacaw_ctx* ctx, const float* psi_k, int64_t P, int64_t nf, int64_t f0, int64_t F,
+                           int64_t nq, const float* psi_ref, const int32_t* q_sel, int64_t n_sel, float* psi_tilde,
+                           void* stream);
+
+/* Intensity of a summed transform: S[p][m][q_j] = |psi_tilde[p][m][j]|^2 with S = 0 at m = 0
+ * (the mean-subtracted transform vanishes there), other q of S zero (TACAW_REDUCE_NONE;
+ * S_out DEVICE float32 [P][F][nq], nq = n_sel without q_sel), or the spectrum image
+ * SI[p][m] = sum_j S (TACAW_REDUCE_DETECTOR; S_out [P][F], FP64 sums). */
+int tacaw_intensity(tacaw_ctx* ctx, const float* psi_tilde, int64_t P, int64_t F, int64_t n_sel,
+                    const int32_t* q_sel, int64_t nq, int32_t reduce, float* S_out, void* stream);
+
 /* ---- serving: requests admitted by device-memory footprint, run concurrently ------------ */
 
 /* One TACAW simulation request: the inputs and output of tacaw_run. */

@@ -135,6 +135,9 @@ def lib():
             "tacaw_dispersion": (C.c_int, [vp, vp, i64, i64, i32, i32, C.c_double, C.c_double, vp, vp, i32, vp,
                                            vp]),
             "tacaw_accumulate": (C.c_int, [vp, vp, i64, C.c_double, vp, vp]),
+            "tacaw_band_points": (C.c_int, [vp, pp, vp, C.POINTER(i64)]),
+            "tacaw_spectrum_partial": (C.c_int, [vp, vp, i64, i64, i64, i64, i64, vp, vp, i64, vp, vp]),
+            "tacaw_intensity": (C.c_int, [vp, vp, i64, i64, i64, vp, i64, i32, vp, vp]),
             "tacaw_spectrum_static": (C.c_int, [vp, i64, i64, i64, vp, vp]),
             "tacaw_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
             "tacaw_request_footprint": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
@@ -160,7 +163,8 @@ def exported_symbols():
             "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_select", "tacaw_profile_end",
             "tacaw_spectrum_static", "tacaw_submit", "tacaw_request_footprint", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
             "tacaw_serving_stats", "tacaw_set_option", "tacaw_spectral_diffraction", "tacaw_dispersion",
-            "tacaw_accumulate", "tacaw_selftest_wait"]
+            "tacaw_accumulate", "tacaw_selftest_wait", "tacaw_band_points", "tacaw_spectrum_partial",
+            "tacaw_intensity"]
 
 
 def _ptr(x):
@@ -313,6 +317,25 @@ def tacaw_dispersion(ctx, S, P, F, ny, nx, Lx, Ly, kx, ky, out, stream=None):
 
 def tacaw_accumulate(ctx, S, n, weight, acc, stream=None):
     return _check(ctx, lib().tacaw_accumulate(ctx, _ptr(S), n, float(weight), _ptr(acc), _stream(stream)))
+
+
+def tacaw_band_points(ctx, params):
+    """The in-band q list (int32 numpy array) of a geometry, as tacaw_run transforms it."""
+    n = C.c_int64()
+    _check(ctx, lib().tacaw_band_points(ctx, C.byref(params), None, C.byref(n)))
+    q = np.zeros(n.value, dtype=np.int32)
+    _check(ctx, lib().tacaw_band_points(ctx, C.byref(params), q.ctypes.data, C.byref(n)))
+    return q
+
+
+def tacaw_spectrum_partial(ctx, psi_k, P, nf, f0, F, nq, psi_ref, q_sel, n_sel, psi_tilde, stream=None):
+    return _check(ctx, lib().tacaw_spectrum_partial(ctx, _ptr(psi_k), P, nf, f0, F, nq, _ptr(psi_ref), _ptr(q_sel),
+                                                    n_sel, _ptr(psi_tilde), _stream(stream)))
+
+
+def tacaw_intensity(ctx, psi_tilde, P, F, n_sel, q_sel, nq, reduce, S_out, stream=None):
+    return _check(ctx, lib().tacaw_intensity(ctx, _ptr(psi_tilde), P, F, n_sel, _ptr(q_sel), nq, reduce, _ptr(S_out),
+                                             _stream(stream)))
 
 
 def tacaw_check(ctx):

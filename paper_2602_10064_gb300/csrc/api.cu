@@ -1140,6 +1140,23 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   return TACAW_OK;
 }
 
+int tacaw_band_points(tacaw_ctx* ctx, const tacaw_params* params, int32_t* q_out, int64_t* n_out) {
+  if (!ctx || !n_out) return TACAW_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  TRY_RC(check_params(ctx, params));
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  GeoCache* g;
+  const int rc = get_geo(ctx, *params, &g);
+  if (rc != TACAW_OK) return rc;
+  *n_out = g->nsel;
+  if (q_out) {
+    e = cudaMemcpy(q_out, g->qsel, sizeof(int32_t) * g->nsel, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "band points copy");
+  }
+  return TACAW_OK;
+}
+
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (!ctx || !name) return TACAW_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);

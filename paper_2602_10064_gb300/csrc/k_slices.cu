@@ -119,6 +119,10 @@ __device__ __forceinline__ auto group_sync(int g) {
   else return BlockSync{};
 }
 
+// CTAs of a column pass: the in-band columns c < W only, C per CTA.  The padding columns up to Wp
+// are never read by a row pass (band_x_col maps no x to them), so they need no transform.
+static int col_blocks(const Band& b, int C) { return (b.W + C - 1) / C; }
+
 // Batch index over (grid.y, grid.z); batches beyond nb return before any barrier.
 __device__ __forceinline__ int batch_index() { return blockIdx.y + gridDim.y * blockIdx.z; }
 static dim3 batch_grid(int gx, int64_t nb) {
@@ -719,8 +723,15 @@ __global__ void __launch_bounds__(ProbeRowCfg<NX>::THREADS, minb_of<K_PROBE_ROW,
 // Shared memory of the slice row pass: the FFT scratch, plus (TF) one stashed t row per group.
 template <int NX, bool TF>
 struct SliceRowSmem {
-  static constexpr int BYTES = SliceRowCfg<NX>::SMEM + (TF ? SliceRowCfg<NX>::G * NX * (int)sizeof(float2) : 0);
+  static constexpr int BYTES = SliceRowCfg<NX>::SMEM + SliceRowCfg<NX>::G * NX * (int)sizeof(float2);
 };
+
+// Asynchronous 8-byte copy global -> shared (completes at cp_async_wait_all of the same thread).
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int NX, bool FIRST, bool PLANE, bool TF>
 __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW, NX, SliceRowCfg<NX>>())
@@ -746,30 +757,38 @@ __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW,
     store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
     return;
   }
-  // TF: inverse-transform t first and stash the row (each thread rereads only its own
-  // positions, so no barrier is needed); only one row of the wave is then live in registers
+  // The transmission row goes to a shared-memory stash before it is used; each thread writes
+  // and rereads only its own positions, so no barrier is needed.  TF: t is inverse-transformed
+  // first (only one row of the wave is then live in registers).  Otherwise the full t row is
+  // copied asynchronously at once, so its load overlaps the wave's load and inverse transform.
   float2* tst = reinterpret_cast<float2*>(smraw + SliceRowCfg<NX>::SMEM) + g * NX;
   if (TF) {
     load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
     fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
 #pragma unroll
     for (int e = 0; e < E; ++e) tst[t + T * e] = v[e];
+  } else {
+    const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
+#pragma unroll
+    for (int e = 0; e < E; ++e) cp_async8(tst + t + T * e, trow + t + T * e);
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  const float2* trow = ttab + ((size_t)(fl * S + s) * ny + y) * NX;
   if (FIRST) {
+    if (!TF) cp_async_wait_all();
     if (PLANE) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = plane_amp * (TF ? tst[t + T * e] : trow[t + T * e]);
+      for (int e = 0; e < E; ++e) v[e] = plane_amp * tst[t + T * e];
     } else {
       const float2* src = psi0 + ((size_t)p * ny + y) * NX;
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = cmul(src[t + T * e], TF ? tst[t + T * e] : trow[t + T * e]);
+      for (int e = 0; e < E; ++e) v[e] = cmul(src[t + T * e], tst[t + T * e]);
     }
   } else {
     load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
     fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
+    if (!TF) cp_async_wait_all();
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], TF ? tst[t + T * e] : trow[t + T * e]);
+    for (int e = 0; e < E; ++e) v[e] = cmul(v[e], tst[t + T * e]);
   }
   fft<NX, -1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
   store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
@@ -919,7 +938,7 @@ template <int NY>
 static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                              float2* Ap, cudaStream_t st) {
   using CC = ColPotCfg<NY>;
-  const dim3 grid = batch_grid(b.Wp / CC::C, nfs);
+  const dim3 grid = batch_grid(col_blocks(b, CC::C), nfs);
   cudaError_t e;
   if (npair == 1) {
     if ((e = prep(k_col_pot<NY, true>, CC::SMEM)) != cudaSuccess) return e;
@@ -965,7 +984,7 @@ static cudaError_t col_t_n(const Geo& g, const Band& b, const float2* Bt, int nf
   using CC = ColTCfg<NY>;
   const cudaError_t e = prep(k_col_t<NY>, CC::SMEM);
   if (e != cudaSuccess) return e;
-  k_col_t<NY><<<batch_grid(b.Wp / CC::C, nfs), CC::THREADS, CC::SMEM, st>>>(g, b, Bt, nfs,
+  k_col_t<NY><<<batch_grid(col_blocks(b, CC::C), nfs), CC::THREADS, CC::SMEM, st>>>(g, b, Bt, nfs,
                                                                                                    scale, At);
   return cudaGetLastError();
 }
@@ -990,7 +1009,7 @@ static cudaError_t probe_col_n(const Geo& g, const Band& ap, const float2* ex, c
   using CC = ProbeColCfg<NY>;
   const cudaError_t e = prep(k_probe_col<NY>, CC::SMEM);
   if (e != cudaSuccess) return e;
-  k_probe_col<NY><<<batch_grid(ap.Wp / CC::C, P), CC::THREADS, CC::SMEM, st>>>(
+  k_probe_col<NY><<<batch_grid(col_blocks(ap, CC::C), P), CC::THREADS, CC::SMEM, st>>>(
       g, ap, ex, ey, chi, P, amp, Bpr);
   return cudaGetLastError();
 }
@@ -1049,7 +1068,7 @@ static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const floa
                                const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st) {
   const int nw = P * nfc;
   using CC = SliceColCfg<NY>;
-  const dim3 grid = batch_grid(b.Wp / CC::C, nw);
+  const dim3 grid = batch_grid(col_blocks(b, CC::C), nw);
   constexpr int TH = CC::THREADS, SM = CC::SMEM;
   cudaError_t e = last ? prep(k_slice_col<NY, true>, SM) : prep(k_slice_col<NY, false>, SM);
   if (e != cudaSuccess) return e;
