@@ -67,7 +67,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
     assert d["config"]["workload"].startswith("c1-") and d["config"]["config"] == "c1"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
-    assert d["cpu_baseline"]["cores"] >= 1 and "2 frame(s) per step" in d["cpu_baseline"]["sample"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "2 frame(s) x 1 probe(s) per step" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
