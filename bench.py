@@ -438,6 +438,8 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=0, help="frames per reference step (0: one per host thread)")
     ap.add_argument("--ref-probes", type=int, default=2, help="probes of a scan per reference step")
     ap.add_argument("--frames", type=int, default=None, help="truncate the trajectory (profiling cases)")
+    ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
+                    help="context option (tacaw_set_option) for the timed runs, e.g. max_chunk_frames=2")
     ap.add_argument("--serving-requests", type=int, default=24, help="requests in the serving run (0: skip)")
     ap.add_argument("--plain-sample", type=int, default=16,
                     help="c5: requests of the stream the plain path is timed on (0: all)")
@@ -469,6 +471,9 @@ def main():
     prec = PRECISIONS[args.precision]
     ctx = T.Context(local)
     ctx.load_form_factors(w.form_Z, w.form_coef)
+    for opt in args.option:
+        name, value = opt.split("=")
+        ctx.set_option(name.strip(), int(value))
     params, probe = T.params_of(w), T.probe_of(w)
     pos = torch.from_numpy(w.pos).cuda()
     Z = torch.from_numpy(w.Z).cuda()
@@ -553,7 +558,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded harmonic-mode trajectory; placeholder Kirkland-form table)",
-        "config": workload_config(w, args.workload, args.precision),
+        "config": dict(workload_config(w, args.workload, args.precision),
+                       **({"options": args.option} if args.option else {})),
         "spectra_per_s": spectra, "px_slices_per_s": value * w.nx * w.ny,
         "step_ms": step_ms,
         "roofline": roofline(prof, args.steps, args.workload, clk.get("sm_mhz")),
