@@ -65,25 +65,6 @@ __device__ __forceinline__ float2 w16(int j) {
   return make_float2(c, SIGN < 0 ? -s : s);
 }
 
-#ifndef TACAW_TW_SPECIAL
-#define TACAW_TW_SPECIAL 0
-#endif
-
-// a * w16^j: a quarter turn (j = 4, 8, 12) is a swap and a sign change, not a product.
-template <int SIGN>
-__device__ __forceinline__ float2 mul_w16(float2 a, int j) {
-  if (TACAW_TW_SPECIAL) {
-    switch (j & 15) {
-      case 0: return a;
-      case 4: return mul_si<SIGN>(a);
-      case 8: return make_float2(-a.x, -a.y);
-      case 12: return mul_si<-SIGN>(a);
-      default: break;
-    }
-  }
-  return cmul(a, w16<SIGN>(j));
-}
-
 template <int SIGN>
 __device__ __forceinline__ void dft2(float2* u) {
   float2 a = u[0], b = u[1];
@@ -141,7 +122,7 @@ __device__ __forceinline__ void dft16(float2* u) {
     dft4<SIGN>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
 #pragma unroll
     for (int k1 = 1; k1 < 4; ++k1)
-      if (n2 > 0) y[n2][k1] = mul_w16<SIGN>(y[n2][k1], n2 * k1);
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w16<SIGN>(n2 * k1));
   }
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
@@ -201,21 +182,6 @@ __device__ __forceinline__ float2 w24(int j) {
   return make_float2(c, SIGN < 0 ? -s : s);
 }
 
-// a * w24^j, quarter turns (j = 6, 12, 18) without a product.
-template <int SIGN>
-__device__ __forceinline__ float2 mul_w24(float2 a, int j) {
-  if (TACAW_TW_SPECIAL) {
-    switch (j % 24) {
-      case 0: return a;
-      case 6: return mul_si<SIGN>(a);
-      case 12: return make_float2(-a.x, -a.y);
-      case 18: return mul_si<-SIGN>(a);
-      default: break;
-    }
-  }
-  return cmul(a, w24<SIGN>(j));
-}
-
 template <int R, int SIGN>
 __device__ __forceinline__ void dft_r(float2* u);
 
@@ -248,14 +214,8 @@ __device__ __forceinline__ void dft32(float2* u) {
     for (int n1 = 0; n1 < 8; ++n1) y[n2][n1] = u[n2 + 4 * n1];
     dft8<SIGN>(y[n2]);
 #pragma unroll
-    for (int k1 = 1; k1 < 8; ++k1) {
-      if (n2 == 0) continue;
-      const int j = (n2 * k1) & 31;
-      if (TACAW_TW_SPECIAL && j == 8) y[n2][k1] = mul_si<SIGN>(y[n2][k1]);
-      else if (TACAW_TW_SPECIAL && j == 16) y[n2][k1] = make_float2(-y[n2][k1].x, -y[n2][k1].y);
-      else if (TACAW_TW_SPECIAL && j == 24) y[n2][k1] = mul_si<-SIGN>(y[n2][k1]);
-      else y[n2][k1] = cmul(y[n2][k1], w32<SIGN>(j));
-    }
+    for (int k1 = 1; k1 < 8; ++k1)
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w32<SIGN>(n2 * k1));
   }
 #pragma unroll
   for (int k1 = 0; k1 < 8; ++k1) {
@@ -282,7 +242,7 @@ __device__ __forceinline__ void dft_ct(float2* u) {
     dft_r<R1, SIGN>(y[n2]);
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1)
-      if (n2 > 0) y[n2][k1] = mul_w24<SIGN>(y[n2][k1], (24 / R) * n2 * k1);
+      if (n2 > 0) y[n2][k1] = cmul(y[n2][k1], w24<SIGN>((24 / R) * n2 * k1));
   }
 #pragma unroll
   for (int k1 = 0; k1 < R1; ++k1) {

@@ -131,10 +131,6 @@ static dim3 batch_grid(int gx, int64_t nb) {
   return dim3((unsigned)gx, y, z);
 }
 
-#ifndef TACAW_BRANCHFREE_ROWS
-#define TACAW_BRANCHFREE_ROWS 0
-#endif
-
 template <int N, int E>
 __device__ __forceinline__ void load_row_compact(float2 (&v)[E], const float2* __restrict__ src, const Band& b,
                                                  int t) {
@@ -142,12 +138,7 @@ __device__ __forceinline__ void load_row_compact(float2 (&v)[E], const float2* _
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int c = band_x_col(b, N, t + T * e);
-    if (TACAW_BRANCHFREE_ROWS) {
-      const float2 val = src[c < 0 ? 0 : c];
-      v[e] = c >= 0 ? val : make_float2(0.f, 0.f);
-    } else {
-      v[e] = c >= 0 ? src[c] : make_float2(0.f, 0.f);
-    }
+    v[e] = c >= 0 ? src[c] : make_float2(0.f, 0.f);
   }
 }
 
@@ -158,8 +149,7 @@ __device__ __forceinline__ void store_row_compact(const float2 (&v)[E], float2* 
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int c = band_x_col(b, N, t + T * e);
-    if (TACAW_BRANCHFREE_ROWS) dst[c < 0 ? b.W : c] = v[e];
-    else if (c >= 0) dst[c] = v[e];
+    if (c >= 0) dst[c] = v[e];
   }
 }
 
