@@ -1281,16 +1281,16 @@ int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, con
   if (precision < TACAW_DFT_FP32 || precision > TACAW_DFT_TF32) return set_err(ctx, TACAW_EINVAL, "bad precision");
   cudaStream_t st = sc.st;
   const int64_t nsel = io.nsel;
-  double2* mean;
-  CK(sc.get(&mean, (size_t)P * nsel));
   const double pfq = (double)P * F * nsel;
-  {
-    ProfScope ps(ctx, "mean_f64", st, pfq * 8 + (double)P * nsel * 16, pfq * 2);
-    CK(launch_mean_f64(psi_k, P, F, io.in_nq, io.in_qsel, nsel, mean, st));
-  }
   const bool det = reduce == TACAW_REDUCE_DETECTOR;
   if (!det && io.out_qsel && nsel < io.out_nq) CK(cudaMemsetAsync(S_out, 0, sizeof(float) * P * F * io.out_nq, st));
   if (precision == TACAW_DFT_FP32) {
+    double2* mean;
+    CK(sc.get(&mean, (size_t)P * nsel));
+    {
+      ProfScope ps(ctx, "mean_f64", st, pfq * 8 + (double)P * nsel * 16, pfq * 2);
+      CK(launch_mean_f64(psi_k, P, F, io.in_nq, io.in_qsel, nsel, mean, st));
+    }
     float2* r;
     CK(sc.get(&r, (size_t)P * F * nsel));
     {
@@ -1312,7 +1312,7 @@ int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, con
     }
     return TACAW_OK;
   }
-  return spectrum_tc(ctx, psi_k, mean, P, F, io, precision, reduce, S_out, sc);
+  return spectrum_tc(ctx, psi_k, P, F, io, precision, reduce, S_out, sc);
 }
 
 }  // namespace tacaw

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -158,14 +159,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// One 128 x 256 tile of D per CTA; tiles are numbered with the row block fastest so that the
-// CTAs running together share their B tile through L2.
+// Persistent: CTA c takes the tiles c, c + gridDim.x, ... of D (128 x 256 each), numbered with
+// the row block fastest so that the CTAs running together share their B tile through L2.  The
+// shared-memory ring, the K chunks and the two TMEM accumulator buffers run on counters that
+// continue across tiles, so the epilogue of one tile overlaps the first MMAs of the next.
 // nphase: 1 (hi*hi) or 3 (hi*hi, hi*lo, lo*hi); nkb: K blocks of 128 bytes per phase.
 template <bool TF32>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_dft_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
              const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int mtiles,
-             int nphase, int nkb, int64_t F, int64_t cpp, int64_t nsel, int64_t out_nq,
+             int64_t tiles, int nphase, int nkb, int64_t F, int64_t cpp, int64_t nsel, int64_t out_nq,
              const int32_t* __restrict__ out_qsel, float* __restrict__ S, double* __restrict__ part,
              int* __restrict__ status) {
   extern __shared__ uint8_t smraw[];
@@ -178,11 +181,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES);
   const uint32_t accf0 = smem_u32(bars + 2 * TC_STAGES), acce0 = smem_u32(bars + 2 * TC_STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tile = blockIdx.x;
-  const int mt = (int)(tile % mtiles);
-  const int64_t nt = tile / mtiles;
-  const int m0 = mt * TC_BM;
-  const int64_t n0 = nt * TC_BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -206,53 +204,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int total = nphase * nkb;  // K blocks; each holds 4 MMAs of 32 bytes of K
+  const int total = nphase * nkb;  // K blocks per tile; each holds 4 MMAs of 32 bytes of K
   const int nchunk = (total + TC_KC - 1) / TC_KC;
 
   if (warp == 0 && lane == 0) {
-    // producer
-    int issued = 0;
-    for (int kb = 0; kb < total; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
-      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, status)) break;
-      const int phase = kb / nkb, kk = kb % nkb;
-      const CUtensorMap* ma = (phase == 2) ? &mAlo : &mAhi;
-      const CUtensorMap* mb = (phase == 1) ? &mBlo : &mBhi;
-      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
-      const int kx = kk * (TC_ROW_BYTES / (TF32 ? 4 : 2));
-      mbar_expect_tx(full0 + 8 * s, TC_STAGE_BYTES);
-      tma_load_2d(sa, ma, kx, m0, full0 + 8 * s);
-      tma_load_2d(sb, mb, kx, (int)n0, full0 + 8 * s);
-      issued = kb + 1;
+    // producer: K block i of the CTA's sequence (all its tiles) goes to stage i % TC_STAGES
+    int64_t i = 0, issued = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      const int m0 = (int)(tile % mtiles) * TC_BM;
+      const int n0 = (int)((tile / mtiles) * TC_BN);
+      for (int kb = 0; kb < total; ++kb, ++i) {
+        const int s = (int)(i % TC_STAGES);
+        const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, status)) {
+          ok = false;
+          break;
+        }
+        const int phase = kb / nkb, kk = kb % nkb;
+        const CUtensorMap* ma = (phase == 2) ? &mAlo : &mAhi;
+        const CUtensorMap* mb = (phase == 1) ? &mBlo : &mBhi;
+        const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
+        const int kx = kk * (TC_ROW_BYTES / (TF32 ? 4 : 2));
+        mbar_expect_tx(full0 + 8 * s, TC_STAGE_BYTES);
+        tma_load_2d(sa, ma, kx, m0, full0 + 8 * s);
+        tma_load_2d(sb, mb, kx, n0, full0 + 8 * s);
+        issued = i + 1;
+      }
     }
     // leave no copy in flight: wait for the last stages this thread armed
-    for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full0 + 8 * (kb % TC_STAGES), (uint32_t)((kb / TC_STAGES) & 1), status);
+    for (int64_t k = (issued > TC_STAGES ? issued - TC_STAGES : 0); k < issued; ++k)
+      mbar_wait(full0 + 8 * (int)(k % TC_STAGES), (uint32_t)((k / TC_STAGES) & 1), status);
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer: chunk c accumulates into TMEM buffer c & 1
+    // MMA issuer: chunk g of the CTA's sequence accumulates into TMEM buffer g & 1
+    int64_t i = 0, g = 0;
     bool ok = true;
-    for (int c = 0; c < nchunk && ok; ++c) {
-      const int b = c & 1;
-      if (c >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)(((c >> 1) - 1) & 1), status)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + (uint32_t)(b * TC_BN);
-      const int kb1 = (c + 1) * TC_KC < total ? (c + 1) * TC_KC : total;
-      for (int kb = c * TC_KC; kb < kb1; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
-        if (!mbar_wait(full0 + 8 * s, ph, status)) {
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      for (int c = 0; c < nchunk && ok; ++c, ++g) {
+        const int b = (int)(g & 1);
+        if (g >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)(((g >> 1) - 1) & 1), status)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
+        const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+        const int kb1 = (c + 1) * TC_KC < total ? (c + 1) * TC_KC : total;
+        for (int kb = c * TC_KC; kb < kb1; ++kb, ++i) {
+          const int s = (int)(i % TC_STAGES);
+          const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
+          if (!mbar_wait(full0 + 8 * s, ph, status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES), sb = sa + TC_A_BYTES;
 #pragma unroll
-        for (int k = 0; k < TC_ROW_BYTES / 32; ++k)
-          tc_mma<TF32>(d, smem_desc_sw128(sa + 32 * k), smem_desc_sw128(sb + 32 * k), (kb - c * TC_KC) | k);
-        tc_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+          for (int k = 0; k < TC_ROW_BYTES / 32; ++k)
+            tc_mma<TF32>(d, smem_desc_sw128(sa + 32 * k), smem_desc_sw128(sb + 32 * k), (kb - c * TC_KC) | k);
+          tc_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+        }
+        if (ok) tc_commit(accf0 + 8 * b);  // this chunk's MMAs complete -> buffer b readable
       }
-      tc_commit(accf0 + 8 * b);  // this chunk's MMAs complete -> buffer b readable
     }
     // no MMA may be in flight when TMEM is released, also after a timeout
     tc_commit(drain);
@@ -260,62 +272,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp >= 2) {
     // accumulators: warp w owns TMEM lanes 32 (w % 4) .. +31 and columns [128 h, 128 h + 128)
     const int e = warp - 2, quarter = warp & 3, half = e >> 2;
-    float acc[TC_EPI_COLS];
-#pragma unroll
-    for (int i = 0; i < TC_EPI_COLS; ++i) acc[i] = 0.f;
     bool ok = true;
-    for (int c = 0; c < nchunk; ++c) {
-      const int b = c & 1;
-      ok = __all_sync(0xffffffffu, ok && mbar_wait(accf0 + 8 * b, (uint32_t)((c >> 1) & 1), status));
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * TC_BN + half * TC_EPI_COLS);
+    int64_t g = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int m0 = (int)(tile % mtiles) * TC_BM;
+      const int64_t n0 = (tile / mtiles) * TC_BN;
+      float acc[TC_EPI_COLS];
 #pragma unroll
-      for (int c0 = 0; c0 < TC_EPI_COLS; c0 += 32) {
-        float v[32];
-        tmem_ld32(base + (uint32_t)c0, v);
+      for (int i = 0; i < TC_EPI_COLS; ++i) acc[i] = 0.f;
+      for (int c = 0; c < nchunk && ok; ++c, ++g) {
+        const int b = (int)(g & 1);
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(accf0 + 8 * b, (uint32_t)((g >> 1) & 1), status));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * TC_BN + half * TC_EPI_COLS);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c0 + i] += v[i];
+        for (int c0 = 0; c0 < TC_EPI_COLS; c0 += 32) {
+          float v[32];
+          tmem_ld32(base + (uint32_t)c0, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[c0 + i] += v[i];
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
-    }
-    // rows m0 + 32 quarter + lane: even lanes hold Re, odd lanes Im of psi~(w); the tile's
-    // columns all belong to probe p (cpp is a multiple of TC_BN)
-    const int m = m0 + 32 * quarter + lane;
-    const int64_t w = m >> 1;
-    const bool writer = ((lane & 1) == 0) && w < F;
-    const int64_t p = n0 / cpp, j0 = n0 - p * cpp + half * TC_EPI_COLS;
-    if (!part) {
-      if (ok) {
+      // rows m0 + 32 quarter + lane: even lanes hold Re, odd lanes Im of psi~(w); the tile's
+      // columns all belong to probe p (cpp is a multiple of TC_BN)
+      const int m = m0 + 32 * quarter + lane;
+      const int64_t w = m >> 1;
+      const bool writer = ((lane & 1) == 0) && w < F;
+      const int64_t p = n0 / cpp, j0 = n0 - p * cpp + half * TC_EPI_COLS;
+      if (!part) {
+        if (ok) {
+#pragma unroll
+          for (int i = 0; i < TC_EPI_COLS; ++i) {
+            const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
+            const float sv = acc[i] * acc[i] + o * o;
+            const int64_t j = j0 + i;
+            if (writer && j < nsel) {
+              const int64_t q = out_qsel ? out_qsel[j] : j;
+              S[((size_t)p * F + w) * out_nq + q] = sv;
+            }
+          }
+        }
+      } else {
+        // detector sum: |psi~|^2 rounded to float as a stored S would be, summed in FP64 over
+        // this thread's columns, then over the two column halves in a fixed order
+        double dsum = 0.0;
 #pragma unroll
         for (int i = 0; i < TC_EPI_COLS; ++i) {
           const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
           const float sv = acc[i] * acc[i] + o * o;
-          const int64_t j = j0 + i;
-          if (writer && j < nsel) {
-            const int64_t q = out_qsel ? out_qsel[j] : j;
-            S[((size_t)p * F + w) * out_nq + q] = sv;
-          }
+          if (j0 + i < nsel) dsum += (double)sv;
         }
-      }
-    } else {
-      // detector sum: |psi~|^2 rounded to float as a stored S would be, summed in FP64 over
-      // this thread's columns, then over the two column halves in a fixed order
-      double dsum = 0.0;
-#pragma unroll
-      for (int i = 0; i < TC_EPI_COLS; ++i) {
-        const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
-        const float sv = acc[i] * acc[i] + o * o;
-        if (j0 + i < nsel) dsum += (double)sv;
-      }
-      if ((lane & 1) == 0) red[half * (TC_BM / 2) + ((32 * quarter + lane) >> 1)] = dsum;
-      // every epilogue warp arrives here, also after a timed-out wait
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
-      if (ok && half == 0 && writer) {
         const int r = (32 * quarter + lane) >> 1;
-        part[(size_t)(n0 / TC_BN) * F + w] = red[r] + red[TC_BM / 2 + r];
+        if ((lane & 1) == 0) red[half * (TC_BM / 2) + r] = dsum;
+        // every epilogue warp arrives here for every tile, also after a timed-out wait
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
+        if (ok && half == 0 && writer) part[(size_t)(n0 / TC_BN) * F + w] = red[r] + red[TC_BM / 2 + r];
+        // the next tile's partial sums reuse red
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
       }
     }
   }
@@ -332,72 +349,87 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Residual split: B_hi/B_lo[J][2n + c] for J = p * nsel + j, from r = psi[p][n][q_j] - mean[p][j],
-// zero for K pad columns.  32 x 32 (j, n) tile per CTA, transposed through shared memory.  The
-// difference is formed exactly as the FP32 pair (r, re) (pair_sub: the FP64 mean as an FP32
-// pair); hi = r rounded to the operand type, lo = (r - hi) + re, where r - hi is exact.
+// Frame mean and residual split in one pass per column block: B_hi/B_lo[J][2n + c] for
+// J = p * cpp + j, from r = psi[p][n][q_j] - mean[p][j], zero for the padding columns j >= nsel
+// and the K pad frames.  A CTA takes 32 columns: 8 threads per column form the frame mean to
+// FP64-class precision (column_pair_sums, combine_pair_sums: the arithmetic of the mean kernel of
+// the FP32 path), then the CTA walks the frames in 32 x 32 (j, n) tiles, transposed through
+// shared memory; the second read of the column block comes from L2.  The difference is formed
+// exactly as the FP32 pair (r, re) (pair_sub: the FP64 mean as an FP32 pair); hi = r rounded to
+// the operand type, lo = (r - hi) + re, where r - hi is exact.
+constexpr int RS_GROUPS = 8;
 template <bool TF32>
-__global__ void __launch_bounds__(256) k_residual_split(const float2* __restrict__ psi, const double2* __restrict__ mean,
-                                                        int64_t F, int64_t nq, const int32_t* __restrict__ qsel,
-                                                        int64_t nsel, int64_t cpp, int64_t P, int kpad2,
-                                                        void* __restrict__ Bhi, void* __restrict__ Blo) {
+__global__ void __launch_bounds__(256) k_mean_residual_split(const float2* __restrict__ psi, int64_t F, int64_t nq,
+                                                             const int32_t* __restrict__ qsel, int64_t nsel,
+                                                             int64_t cpp, int kpad2, void* __restrict__ Bhi,
+                                                             void* __restrict__ Blo) {
+  __shared__ float4 part[RS_GROUPS][32];
+  __shared__ float4 msplit[32];  // mean as FP32 pairs (hi.x, lo.x, hi.y, lo.y)
   __shared__ float2 hs[32][33], ls[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t J0 = (int64_t)blockIdx.x * 32;
-  const int64_t n0 = (int64_t)blockIdx.y * 32;
-  const int64_t ncols = P * cpp;
-  // phase 1: coalesced along j; columns j >= nsel of a probe (padding) are zero
-  const int64_t J = J0 + tx;
-  int64_t p = 0, j = 0, q = 0;
-  float mxh = 0.f, mxl = 0.f, myh = 0.f, myl = 0.f;
-  const bool live = J < ncols && J - (J / cpp) * cpp < nsel;
-  if (live) {
-    p = J / cpp;
-    j = J - p * cpp;
-    q = qsel ? qsel[j] : j;
-    const double2 mu = mean[(size_t)p * nsel + j];
-    split_double(mu.x, mxh, mxl);
-    split_double(mu.y, myh, myl);
-  }
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t n = n0 + r;
-    float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
-    if (live && n < F) {
-      const float2 v = psi[((size_t)p * F + n) * nq + q];
-      float rx, ex, ry, ey;
-      pair_sub(v.x, mxh, mxl, rx, ex);
-      pair_sub(v.y, myh, myl, ry, ey);
-      if (TF32) {
-        const float ah = to_tf32(rx), bh = to_tf32(ry);
-        h = make_float2(ah, bh);
-        l = make_float2(to_tf32(__fadd_rn(__fsub_rn(rx, ah), ex)), to_tf32(__fadd_rn(__fsub_rn(ry, bh), ey)));
-      } else {
-        h = make_float2(__bfloat162float(__float2bfloat16_rn(rx)), __bfloat162float(__float2bfloat16_rn(ry)));
-        l = make_float2(__fadd_rn(__fsub_rn(rx, h.x), ex), __fadd_rn(__fsub_rn(ry, h.y), ey));
-      }
-    }
-    hs[r][tx] = h;
-    ls[r][tx] = l;
+  // columns j >= nsel of a probe (padding) are zero; a block of 32 lies inside one probe
+  const int64_t J = J0 + tx, p = J / cpp, j = J - p * cpp;
+  const bool live = j < nsel;
+  const int64_t q = live ? (qsel ? qsel[j] : j) : 0;
+  const float2* col = psi + (size_t)p * F * nq + q;
+  part[ty][tx] = live ? column_pair_sums<RS_GROUPS>(col, F, nq, ty) : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  if (ty == 0) {
+    float4 c[RS_GROUPS];
+#pragma unroll
+    for (int k = 0; k < RS_GROUPS; ++k) c[k] = part[k][tx];
+    const double2 mu = combine_pair_sums<RS_GROUPS>(c, F);
+    float4 m;
+    split_double(mu.x, m.x, m.y);
+    split_double(mu.y, m.z, m.w);
+    msplit[tx] = m;
   }
   __syncthreads();
-  // phase 2: each warp writes rows J (contiguous along n)
-  for (int c = ty; c < 32; c += 8) {
-    const int64_t Jw = J0 + c;
-    const int64_t n = n0 + tx;
-    if (Jw >= ncols || 2 * n >= kpad2) continue;
-    const float2 h = hs[tx][c], l = ls[tx][c];
-    if (TF32) {
-      reinterpret_cast<float2*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = h;
-      reinterpret_cast<float2*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = l;
-    } else {
-      __nv_bfloat162 hh, ll;
-      hh.x = __float2bfloat16_rn(h.x);
-      hh.y = __float2bfloat16_rn(h.y);
-      ll.x = __float2bfloat16_rn(l.x);
-      ll.y = __float2bfloat16_rn(l.y);
-      reinterpret_cast<__nv_bfloat162*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = hh;
-      reinterpret_cast<__nv_bfloat162*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = ll;
+  const float4 m = msplit[tx];
+  for (int64_t n0 = 0; 2 * n0 < kpad2; n0 += 32) {
+    // phase 1: coalesced along j
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t n = n0 + r;
+      float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+      if (live && n < F) {
+        const float2 v = col[(size_t)n * nq];
+        float rx, ex, ry, ey;
+        pair_sub(v.x, m.x, m.y, rx, ex);
+        pair_sub(v.y, m.z, m.w, ry, ey);
+        if (TF32) {
+          const float ah = to_tf32(rx), bh = to_tf32(ry);
+          h = make_float2(ah, bh);
+          l = make_float2(to_tf32(__fadd_rn(__fsub_rn(rx, ah), ex)), to_tf32(__fadd_rn(__fsub_rn(ry, bh), ey)));
+        } else {
+          h = make_float2(__bfloat162float(__float2bfloat16_rn(rx)), __bfloat162float(__float2bfloat16_rn(ry)));
+          l = make_float2(__fadd_rn(__fsub_rn(rx, h.x), ex), __fadd_rn(__fsub_rn(ry, h.y), ey));
+        }
+      }
+      hs[r][tx] = h;
+      ls[r][tx] = l;
     }
+    __syncthreads();
+    // phase 2: each warp writes rows J (contiguous along n)
+    for (int c = ty; c < 32; c += 8) {
+      const int64_t Jw = J0 + c;
+      const int64_t n = n0 + tx;
+      if (2 * n >= kpad2) continue;
+      const float2 h = hs[tx][c], l = ls[tx][c];
+      if (TF32) {
+        reinterpret_cast<float2*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = h;
+        reinterpret_cast<float2*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = l;
+      } else {
+        __nv_bfloat162 hh, ll;
+        hh.x = __float2bfloat16_rn(h.x);
+        hh.y = __float2bfloat16_rn(h.y);
+        ll.x = __float2bfloat16_rn(l.x);
+        ll.y = __float2bfloat16_rn(l.y);
+        reinterpret_cast<__nv_bfloat162*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = hh;
+        reinterpret_cast<__nv_bfloat162*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = ll;
+      }
+    }
+    __syncthreads();  // the tile buffers are refilled for the next frames
   }
 }
 
@@ -537,8 +569,8 @@ int get_dft_operands(tacaw_ctx* ctx, int64_t F, bool tf32, int64_t kpad, void** 
   return TACAW_OK;
 }
 
-int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, const SpecIO& io,
-                int32_t precision, int32_t reduce, float* S, Scratch& sc) {
+int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, const SpecIO& io, int32_t precision,
+                int32_t reduce, float* S, Scratch& sc) {
   const bool tf32 = precision == TACAW_DFT_TF32X3 || precision == TACAW_DFT_TF32;
   const int nphase = (precision == TACAW_DFT_BF16X3 || precision == TACAW_DFT_TF32X3) ? 3 : 1;
   const int esz = tf32 ? 4 : 2;
@@ -557,18 +589,16 @@ int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_
   if (e == cudaSuccess) e = sc.get(&Blo, (size_t)ncols * kpad * esz);
   if (e != cudaSuccess) return cuda_err(ctx, e, "spectrum operand scratch");
   {
-    ProfScope ps(ctx, tf32 ? "residual_split_tf32" : "residual_split_bf16", sc.st,
-                 (double)P * F * nsel * 8 + (double)ncols * kpad * esz * 2, (double)P * F * nsel * 4);
-    const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((kpad / 2 + 31) / 32));
-    if (grid.y > 65535) return set_err(ctx, TACAW_EINVAL, "too many frames");
+    ProfScope ps(ctx, tf32 ? "mean_residual_split_tf32" : "mean_residual_split_bf16", sc.st,
+                 (double)P * F * nsel * 8 + (double)ncols * kpad * esz * 2, (double)P * F * nsel * 6);
     if (tf32)
-      k_residual_split<true><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, io.in_nq, io.in_qsel, nsel, cpp, P, (int)kpad,
-                                                      Bhi, Blo);
+      k_mean_residual_split<true><<<(unsigned)(ncols / 32), 256, 0, sc.st>>>(psi_k, F, io.in_nq, io.in_qsel, nsel, cpp,
+                                                                            (int)kpad, Bhi, Blo);
     else
-      k_residual_split<false><<<grid, 256, 0, sc.st>>>(psi_k, mean, F, io.in_nq, io.in_qsel, nsel, cpp, P,
-                                                       (int)kpad, Bhi, Blo);
+      k_mean_residual_split<false><<<(unsigned)(ncols / 32), 256, 0, sc.st>>>(psi_k, F, io.in_nq, io.in_qsel, nsel,
+                                                                             cpp, (int)kpad, Bhi, Blo);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_err(ctx, e, "k_residual_split");
+    if (e != cudaSuccess) return cuda_err(ctx, e, "k_mean_residual_split");
   }
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
   if (!make_map(&mAhi, Ahi, tf32, 2 * F, kpad, TC_BM) || !make_map(&mAlo, Alo, tf32, 2 * F, kpad, TC_BM) ||
@@ -577,7 +607,10 @@ int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_
   const int mtiles = (int)((2 * F + TC_BM - 1) / TC_BM);
   const int64_t ntiles = ncols / TC_BN;
   const int64_t tiles = (int64_t)mtiles * ntiles;
-  if (tiles > ((int64_t)1 << 31) - 1) return set_err(ctx, TACAW_EINVAL, "spectrum too large");
+  int nsm = 0;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaDeviceGetAttribute");
+  const unsigned ctas = (unsigned)std::min<int64_t>(tiles, std::max(nsm, 1));  // persistent: one CTA per SM
   const int nkb = (int)(kpad / kblk);
   double* part = nullptr;
   const bool det = reduce == TACAW_REDUCE_DETECTOR;
@@ -594,13 +627,12 @@ int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_
     ProfScope ps(ctx, tf32 ? "dft_tc_tf32" : "dft_tc_bf16", sc.st,
                  (double)ncols * kpad * esz * (nphase > 1 ? 2 : 1) + out_bytes, flops);
     if (tf32)
-      k_dft_tc<true><<<(unsigned)tiles, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, nphase, nkb, F,
-                                                                     cpp, nsel, io.out_nq, io.out_qsel, S, part,
-                                                                     ctx->d_status);
+      k_dft_tc<true><<<ctas, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, tiles, nphase, nkb, F,
+                                                          cpp, nsel, io.out_nq, io.out_qsel, S, part, ctx->d_status);
     else
-      k_dft_tc<false><<<(unsigned)tiles, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, nphase, nkb,
-                                                                      F, cpp, nsel, io.out_nq, io.out_qsel, S, part,
-                                                                      ctx->d_status);
+      k_dft_tc<false><<<ctas, TC_THREADS, TC_SMEM, sc.st>>>(mAhi, mAlo, mBhi, mBlo, mtiles, tiles, nphase, nkb,
+                                                           F, cpp, nsel, io.out_nq, io.out_qsel, S, part,
+                                                           ctx->d_status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_dft_tc");
   }

@@ -23,38 +23,18 @@ __global__ void __launch_bounds__(MEAN_COLS * MEAN_GROUPS)
   const int tx = threadIdx.x % MEAN_COLS, g = threadIdx.x / MEAN_COLS;
   const int64_t j = blockIdx.x * (int64_t)MEAN_COLS + tx;
   const int64_t p = blockIdx.y;
-  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+  float4 ps = make_float4(0.f, 0.f, 0.f, 0.f);
   if (j < nsel) {
     const int64_t q = qsel ? qsel[j] : j;
-    const float2* col = psi + (size_t)p * F * nq + q;
-    int64_t n = g;
-    for (; n + 3 * MEAN_GROUPS < F; n += 4 * MEAN_GROUPS) {
-      float2 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = col[(size_t)(n + u * MEAN_GROUPS) * nq];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        pair_add(hx, lx, v[u].x);
-        pair_add(hy, ly, v[u].y);
-      }
-    }
-    for (; n < F; n += MEAN_GROUPS) {
-      const float2 v = col[(size_t)n * nq];
-      pair_add(hx, lx, v.x);
-      pair_add(hy, ly, v.y);
-    }
+    ps = column_pair_sums<MEAN_GROUPS>(psi + (size_t)p * F * nq + q, F, nq, g);
   }
-  part[g][tx] = make_float4(hx, lx, hy, ly);
+  part[g][tx] = ps;
   __syncthreads();
   if (g == 0 && j < nsel) {
-    double sx = 0.0, sy = 0.0;
+    float4 col[MEAN_GROUPS];
 #pragma unroll
-    for (int k = 0; k < MEAN_GROUPS; ++k) {
-      const float4 a = part[k][tx];
-      sx += (double)a.x + (double)a.y;
-      sy += (double)a.z + (double)a.w;
-    }
-    mean[(size_t)p * nsel + j] = make_double2(sx / (double)F, sy / (double)F);
+    for (int k = 0; k < MEAN_GROUPS; ++k) col[k] = part[k][tx];
+    mean[(size_t)p * nsel + j] = combine_pair_sums<MEAN_GROUPS>(col, F);
   }
 }
 

@@ -135,8 +135,8 @@ int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out);
 // S: the full S (TACAW_REDUCE_NONE, written at the SpecIO output positions only) or the
 // spectrum image SI[P][F] (TACAW_REDUCE_DETECTOR: the sum over the nsel columns, fused into the
 // tensor-core epilogue).
-int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, const double2* mean, int64_t P, int64_t F, const SpecIO& io,
-                int32_t precision, int32_t reduce, float* S, Scratch& sc);
+int spectrum_tc(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, const SpecIO& io, int32_t precision,
+                int32_t reduce, float* S, Scratch& sc);
 // The whole time transform (mean, residual, DFT, |.|^2, optional detector sum) on P probes.
 int spectrum_impl(tacaw_ctx* ctx, const float2* psi_k, int64_t P, int64_t F, const SpecIO& io, int32_t precision,
                   int32_t reduce, float* S_out, Scratch& sc);

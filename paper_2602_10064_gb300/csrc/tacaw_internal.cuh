@@ -64,6 +64,44 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
   two_sum(hi, x, s, e);
   two_sum(s, __fadd_rn(lo, e), hi, lo);
 }
+// Frame mean of one column to FP64-class precision, in two steps shared by the kernels that
+// need it.  column_pair_sums: the thread of group g (of GROUPS) sums the frames n = g, g + GROUPS,
+// ... of col[n * stride] as an FP32 pair per component, in frame order, four loads in flight;
+// returns (hi.x, lo.x, hi.y, lo.y).  combine_pair_sums: the GROUPS pairs added in FP64 in group
+// order and divided by F.  Over n frames a pair loses at most about n 2^-48 of its largest
+// partial sum (FP64 summation: n 2^-53).
+template <int GROUPS>
+__device__ __forceinline__ float4 column_pair_sums(const float2* __restrict__ col, int64_t F, int64_t stride, int g) {
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+  int64_t n = g;
+  for (; n + 3 * GROUPS < F; n += 4 * GROUPS) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = col[(size_t)(n + u * GROUPS) * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pair_add(hx, lx, v[u].x);
+      pair_add(hy, ly, v[u].y);
+    }
+  }
+  for (; n < F; n += GROUPS) {
+    const float2 v = col[(size_t)n * stride];
+    pair_add(hx, lx, v.x);
+    pair_add(hy, ly, v.y);
+  }
+  return make_float4(hx, lx, hy, ly);
+}
+template <int GROUPS>
+__device__ __forceinline__ double2 combine_pair_sums(const float4 (&part)[GROUPS], int64_t F) {
+  double sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int k = 0; k < GROUPS; ++k) {
+    sx += (double)part[k].x + (double)part[k].y;
+    sy += (double)part[k].z + (double)part[k].w;
+  }
+  return make_double2(sx / (double)F, sy / (double)F);
+}
+
 // The FP64 value m as an FP32 pair: hi = fl32(m), lo = fl32(m - hi) (m - hi is exact in FP64).
 __device__ __forceinline__ void split_double(double m, float& hi, float& lo) {
   hi = (float)m;
