@@ -40,8 +40,9 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload(name, seed_offset=0, frames=None):
-    """The named configuration; frames (for small profiling cases) truncates the trajectory."""
+def make_workload(name, seed_offset=0, frames=None, probes=None):
+    """The named configuration; frames and probes (for small profiling cases) truncate the
+    trajectory and the probe scan."""
     import workloads
     if name == "c1":
         w = workloads.diamond_si(n_frames=frames or 64, seed=1 + seed_offset, name="c1-diamond-si-64x128sq")
@@ -55,6 +56,8 @@ def make_workload(name, seed_offset=0, frames=None):
         w = workloads.minimal_example_si(n_frames=frames or 200, seed=6 + seed_offset)
     else:
         raise SystemExit(f"unknown workload {name}")
+    if probes and w.alpha_mrad > 0 and probes < w.n_probes:
+        w.probes = w.probes[:probes]
     return w
 
 
@@ -316,19 +319,22 @@ FULL_MIX = dict(grids=(128, 256, 512, 1024), frames=(64, 128, 256, 512, 1024), s
                 scans=(4, 16), p_plane=0.5)
 
 
-def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm=True, plain_sample=None):
+def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm=True, plain_sample=None,
+                n_geometries=None):
     """Serve n_requests seeded requests arriving as a Poisson stream at rate_factor x the
     measured batched capacity; compare with the plain path (requests one by one).  Plane-wave
     requests return the full S, probe scans the detector-summed spectrum image.
     mix: request ranges (SERVING_MIX or FULL_MIX); warm: run every request once first (tables,
     operands, pools); plain_sample: time the plain path on a seeded sample of that many requests
-    and extrapolate it to the whole stream by pixel-slice work (None: every request)."""
+    and extrapolate it to the whole stream by pixel-slice work (None: every request);
+    n_geometries: draw the requests from that many geometries (repeated screening), and also
+    time the batched capacity without coalescing same-geometry requests."""
     import numpy as np
     import torch
 
     import workloads
     mix = SERVING_MIX if mix is None else mix
-    specs = workloads.request_stream(n_requests, seed=seed, rate_hz=1.0, **mix)
+    specs = workloads.request_stream(n_requests, seed=seed, rate_hz=1.0, n_geometries=n_geometries, **mix)
     ws = [workloads.request_workload(sp) for sp in specs]
     fz, fc = workloads.placeholder_form_factors(sorted(set(int(z) for w in ws for z in w.Z)))
     reqs = []
@@ -349,6 +355,8 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm
         w = r["w"]
         T.tacaw_run(ctx.h, T.params_of(w), r["pos"], r["Z"], w.n_atoms, w.n_frames, r["pr"], prec, r["red"], r["out"])
 
+    batch = []  # requests in the run each request was part of (coalescing), last serve() call
+
     def serve(prec, arrivals):
         tickets = []
         t0 = time.perf_counter()
@@ -361,11 +369,13 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm
                                  r["out"])
             tickets.append(T.tacaw_submit(ctx.h, req))
         lat, first, last = [], None, None
+        batch.clear()
         for t in tickets:
             rc, res = T.tacaw_wait(ctx.h, t, 3600.0)
             if rc != T.TACAW_OK:
                 raise RuntimeError(f"serving request failed: {rc}")
             lat.append(res.t_done - res.t_submit)
+            batch.append(res.batched)
             first = res.t_submit if first is None else min(first, res.t_submit)
             last = res.t_done if last is None else max(last, res.t_done)
         return lat, last - first
@@ -393,10 +403,16 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm
     extrap = len(sample) < len(reqs)
     plain_s = plain_sample_s * (sum(pxwork(r) for r in reqs) / sum(pxwork(reqs[i]) for i in sample))
     # batched capacity: everything submitted at once
+    cap_nocoal_s = None
+    if n_geometries:
+        ctx.set_option("max_coalesce", 1)
+        _, cap_nocoal_s = serve(T.DFT_BF16X3, [0.0] * len(reqs))
+        ctx.set_option("max_coalesce", 16)
     _, cap_s = serve(T.DFT_BF16X3, [0.0] * len(reqs))
     rate = rate_factor * len(reqs) / cap_s
     arrivals = [sp.arrival_s / rate for sp in specs]
     lat, span = serve(T.DFT_BF16X3, arrivals)
+    coalesced = sum(1 for b in batch if b > 1)
     ctx.check()
     ctx.close()
     pct = lambda x, q: float(np.percentile(np.asarray(x), q))
@@ -418,6 +434,10 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm
         "served_rate_vs_plain": (spectra / span) / (spectra / plain_s),
         "precision": "bf16x3 served, fp32 plain (both within 1e-4 of the oracle in the tests)",
         "warmed": warm,
+        "coalesced_requests": coalesced, "mean_run_size": float(np.mean(batch)) if batch else 1.0,
+        **({"geometries": n_geometries,
+            "capacity_without_coalescing_spectra_per_s": spectra / cap_nocoal_s,
+            "coalescing_speedup": cap_nocoal_s / cap_s} if n_geometries else {}),
     }
 
 
@@ -438,9 +458,14 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=0, help="frames per reference step (0: one per host thread)")
     ap.add_argument("--ref-probes", type=int, default=2, help="probes of a scan per reference step")
     ap.add_argument("--frames", type=int, default=None, help="truncate the trajectory (profiling cases)")
+    ap.add_argument("--probes", type=int, default=None, help="truncate the probe scan (profiling cases)")
     ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
                     help="context option (tacaw_set_option) for the timed runs, e.g. max_chunk_frames=2")
     ap.add_argument("--serving-requests", type=int, default=24, help="requests in the serving run (0: skip)")
+    ap.add_argument("--serving-mix", default="full", choices=["full", "small"],
+                    help="c5: the configuration's full request ranges, or the small mix of the default line")
+    ap.add_argument("--serving-geometries", type=int, default=0,
+                    help="c5: draw the requests from this many geometries (repeated screening; 0: all distinct)")
     ap.add_argument("--plain-sample", type=int, default=16,
                     help="c5: requests of the stream the plain path is timed on (0: all)")
     args = ap.parse_args()
@@ -467,7 +492,7 @@ def main():
         dist.barrier()
     import paper_2602_10064_gb300 as T
 
-    w = make_workload(args.workload, seed_offset=rank_seed_offset(rank), frames=args.frames)
+    w = make_workload(args.workload, seed_offset=rank_seed_offset(rank), frames=args.frames, probes=args.probes)
     prec = PRECISIONS[args.precision]
     ctx = T.Context(local)
     ctx.load_form_factors(w.form_Z, w.form_coef)
@@ -598,8 +623,9 @@ def main_serving(args, rank, world, local):
     n = args.serving_requests if args.serving_requests > 24 else 200
     clocks = ClockSampler(local)
     clocks.start()
-    r = run_serving(T, n, seed=5 + 1000 * rank, device=local, mix=FULL_MIX, warm=False,
-                    plain_sample=args.plain_sample or None)
+    mix = FULL_MIX if args.serving_mix == "full" else SERVING_MIX
+    r = run_serving(T, n, seed=5 + 1000 * rank, device=local, mix=mix, warm=False,
+                    plain_sample=args.plain_sample or None, n_geometries=args.serving_geometries or None)
     clk = clocks.stop()
     if rank != 0:
         return
@@ -608,7 +634,9 @@ def main_serving(args, rank, world, local):
         "warmup": 1, "ms_per_step": r["wave_slice_steps"] / r["wave_slice_steps_per_s"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic request stream (seeded cubic/rocksalt cells, Poisson arrivals)",
-        "config": {"workload": f"c5-serving-{n}-requests", "mix": r["mix"]}, "serving": r, "clocks": clk,
+        "config": {"workload": f"c5-serving-{n}-requests" + (f"-{args.serving_geometries}-geometries"
+                                                              if args.serving_geometries else ""),
+                   "mix": r["mix"]}, "serving": r, "clocks": clk,
         "spectra_per_s": r["spectra_per_s"], "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"]}))
 
 

@@ -243,7 +243,7 @@ typedef struct tacaw_request {
 /* State of a request.  Times are seconds on the library's monotonic clock. */
 typedef struct tacaw_result {
   int32_t status;             /* TACAW_PENDING while queued or running, then TACAW_OK or an error */
-  int32_t pad_;
+  int32_t batched;            /* requests in the run this one was part of (1: alone; see tacaw_submit) */
   uint64_t footprint_bytes;   /* device memory reserved for the request while it runs */
   double t_submit, t_admit, t_done;
 } tacaw_result;
@@ -253,7 +253,11 @@ typedef struct tacaw_result {
  * their footprints fit the budget and one of the context's serving streams is free, and runs
  * each on its own stream, so admitted requests overlap on the GPU; later requests are admitted
  * as memory frees up.  A request that does not fit can be overtaken by smaller ones at most 8
- * times.  *ticket identifies the request. */
+ * times.  Queued requests of the same geometry (parameters, probes, frame and atom counts,
+ * species, arithmetic and output; positions may differ) are coalesced, up to 16 (option
+ * "max_coalesce"), into one run
+ * whose launches cover all of them; each result is the same, bit for bit, as alone.  *ticket
+ * identifies the request. */
 int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket);
 
 /* Device bytes the request would reserve while it runs (its admission footprint), without
@@ -312,8 +316,9 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * S slices unless that would leave a slice launch with fewer than "min_wave_rows" wave rows,
  * default 65536).  "max_run_bytes": bound on the scratch of one run (0 = automatic: half the
  * context's budget, at most 64 GiB); probes are propagated and transformed in blocks sized to
- * it.  "max_probe_block": cap on the probes of one block (0 = no cap).  Results do not depend on
- * these options.  EINVAL for an unknown name or a bad value. */
+ * it.  "max_probe_block": cap on the probes of one block (0 = no cap).  "max_coalesce": the most
+ * queued serving requests of one geometry coalesced into one run (default 16; 1 = none).
+ * Results do not depend on these options.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 
 /* Wait for all work on the context's device, then report what the context's kernels flagged

@@ -73,7 +73,7 @@ class Request(C.Structure):
 
 
 class Result(C.Structure):
-    _fields_ = [("status", C.c_int32), ("pad_", C.c_int32), ("footprint_bytes", C.c_uint64),
+    _fields_ = [("status", C.c_int32), ("batched", C.c_int32), ("footprint_bytes", C.c_uint64),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
 
 

@@ -152,6 +152,54 @@ ProfScope::~ProfScope() {
   if (cudaEventRecord(rec.b, st) == cudaSuccess) ctx->prof.recs.push_back(rec);
 }
 
+constexpr size_t kStagingBytes = (size_t)32 << 20;
+
+cudaError_t staged_copy(tacaw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  PinnedRing& R = ctx->staging;
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  if (need > kStagingBytes) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  if (!R.base) {
+    const cudaError_t e = cudaMallocHost((void**)&R.base, kStagingBytes);
+    if (e != cudaSuccess) return e;
+    R.cap = kStagingBytes;
+    R.head = 0;
+  }
+  // retire the regions whose copies have completed (oldest first)
+  while (!R.inflight.empty() && cudaEventQuery(R.inflight.front().done) == cudaSuccess) {
+    R.free_events.push_back(R.inflight.front().done);
+    R.inflight.erase(R.inflight.begin());
+  }
+  cudaGetLastError();  // a not-ready query is not an error
+  size_t off = R.head + need <= R.cap ? R.head : 0;  // wrap to the start when the tail is short
+  // wait for (and retire) the in-flight regions that overlap [off, off + need)
+  for (size_t i = 0; i < R.inflight.size();) {
+    const PinnedRing::Span& sp = R.inflight[i];
+    if (sp.off < off + need && off < sp.end) {
+      const cudaError_t e = cudaEventSynchronize(sp.done);
+      if (e != cudaSuccess) return e;
+      R.free_events.push_back(sp.done);
+      R.inflight.erase(R.inflight.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+  std::memcpy(R.base + off, src, bytes);
+  cudaError_t e = cudaMemcpyAsync(dst, R.base + off, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev;
+  if (!R.free_events.empty()) {
+    ev = R.free_events.back();
+    R.free_events.pop_back();
+  } else if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+    return e;
+  }
+  if ((e = cudaEventRecord(ev, st)) != cudaSuccess) return e;
+  R.inflight.push_back({off, off + need, ev});
+  R.head = off + need;
+  return cudaSuccess;
+}
+
 int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return TACAW_OK;
   if (e == cudaErrorMemoryAllocation) return set_err(c, TACAW_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
@@ -345,8 +393,10 @@ int get_geo(tacaw_ctx* ctx, const tacaw_params& p, GeoCache** out) {
     const Geo geo{nx, ny, ctx->tw};
     CK(launch_build_mtab(geo, g->band, g->npair, nslot, g->coef_slots, g->phix, g->phiy, Lx, Ly,
                          kirkland_pref() / (Lx * Ly), g->mtab, 0));
-    CK(cudaDeviceSynchronize());
   }
+  // the tables are complete (copies and the table kernel on the legacy stream) before any
+  // stream uses them; other streams' work is not waited for
+  CK(cudaStreamSynchronize(0));
   g->ff_version = ctx->ff_version;
   *out = g.get();
   ctx->geos[key] = std::move(g);
@@ -368,6 +418,7 @@ int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out) {
   float2* d;
   TRY_RC(owned_alloc(ctx, &d, F));
   CK(cudaMemcpy(d, h.data(), sizeof(float2) * F, cudaMemcpyHostToDevice));
+  CK(cudaStreamSynchronize(0));  // the copy has landed before any stream reads the table
   ctx->time_tw[F] = d;
   *out = d;
   return TACAW_OK;
@@ -445,7 +496,8 @@ int tacaw_create(tacaw_ctx** out, int32_t device, uint64_t hbm_budget_bytes) {
   if (owned_alloc(ctx, &ctx->tw, tw.size()) != TACAW_OK ||
       cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       owned_alloc(ctx, &ctx->d_status, 1) != TACAW_OK || cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
-      owned_alloc(ctx, &ctx->d_zslot, 256) != TACAW_OK || cudaMemset(ctx->d_zslot, 0xff, 256) != cudaSuccess) {
+      owned_alloc(ctx, &ctx->d_zslot, 256) != TACAW_OK || cudaMemset(ctx->d_zslot, 0xff, 256) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
     for (void* p : ctx->owned) cudaFree(p);
     delete ctx;
     return TACAW_ECUDA;
@@ -459,6 +511,9 @@ int tacaw_destroy(tacaw_ctx* ctx) {
   cudaSetDevice(ctx->device);
   serving_shutdown(ctx);
   cudaDeviceSynchronize();
+  for (auto& sp : ctx->staging.inflight) cudaEventDestroy(sp.done);
+  for (cudaEvent_t ev : ctx->staging.free_events) cudaEventDestroy(ev);
+  if (ctx->staging.base) cudaFreeHost(ctx->staging.base);
   for (void* p : ctx->owned) cudaFree(p);
   delete ctx;
   return TACAW_OK;
@@ -484,6 +539,7 @@ int tacaw_load_form_factors(tacaw_ctx* ctx, const int32_t* Z, const double* coef
   for (int i = 0; i < nZ; ++i) lut[Z[i]] = (int8_t)i;
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemcpy(ctx->d_zslot, lut.data(), 256, cudaMemcpyHostToDevice));
+  CK(cudaStreamSynchronize(0));  // the table has landed before any stream reads it
   ctx->ffZ.assign(Z, Z + nZ);
   ctx->ffcoef.assign(coef, coef + 12 * (size_t)nZ);
   ctx->ff_version++;
@@ -525,8 +581,8 @@ int make_slots(tacaw_ctx* ctx, const int32_t* Z, int64_t A, bool z_on_device, bo
   }
   CK(sc.get(d_slot, A));
   if (A > 0) {
-    // from pageable memory: the call returns once hs is staged, so hs may go out of scope
-    CK(cudaMemcpyAsync(*d_slot, hs.data(), A, cudaMemcpyHostToDevice, sc.st));
+    // through the pinned ring: asynchronous, and hs may go out of scope at once
+    CK(staged_copy(ctx, *d_slot, hs.data(), A, sc.st));
   }
   return TACAW_OK;
 }
@@ -716,16 +772,16 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
   float2 *d_ex, *d_ey, *Bpr, *d_chi = nullptr;
   if (!chi.empty()) {
     CK(sc.get(&d_chi, chi.size()));
-    CK(cudaMemcpyAsync(d_chi, chi.data(), sizeof(float2) * chi.size(), cudaMemcpyHostToDevice, sc.st));
+    CK(staged_copy(ctx, d_chi, chi.data(), sizeof(float2) * chi.size(), sc.st));
   }
   CK(sc.get(&d_nb, Wp));
   CK(sc.get(&d_ex, ex.size()));
   CK(sc.get(&d_ey, ey.size()));
   CK(sc.get(&Bpr, (size_t)P * ny * Wp));
   CK(sc.get(psi0, (size_t)P * ny * nx));
-  CK(cudaMemcpyAsync(d_nb, nb.data(), sizeof(int) * Wp, cudaMemcpyHostToDevice, sc.st));
-  CK(cudaMemcpyAsync(d_ex, ex.data(), sizeof(float2) * ex.size(), cudaMemcpyHostToDevice, sc.st));
-  CK(cudaMemcpyAsync(d_ey, ey.data(), sizeof(float2) * ey.size(), cudaMemcpyHostToDevice, sc.st));
+  CK(staged_copy(ctx, d_nb, nb.data(), sizeof(int) * Wp, sc.st));
+  CK(staged_copy(ctx, d_ex, ex.data(), sizeof(float2) * ex.size(), sc.st));
+  CK(staged_copy(ctx, d_ey, ey.data(), sizeof(float2) * ey.size(), sc.st));
   const Band ap{W, Wp, mb, d_nb};
   const Geo geo{nx, ny, ctx->tw};
   {
@@ -855,13 +911,16 @@ uint64_t run_cap(const tacaw_ctx* ctx) {
   return std::min<uint64_t>(ctx->budget / 2, (uint64_t)64 << 30);
 }
 
-RunPlan run_plan(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t F, int64_t A,
-                 int32_t precision, int32_t reduce) {
+// R trajectories of F frames each can run together, stacked along the frame axis (R F frames
+// through the multislice; R time transforms of F frames per probe).
+RunPlan run_plan(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g, int P, int64_t Fr, int64_t A,
+                 int32_t precision, int32_t reduce, int R) {
   RunPlan pl;
+  const int64_t F = Fr * R;  // frames through the multislice
   const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
   const double fixed = (double)F * A * 44 + (double)F * (S + 1) * 4 + (double)F * S * (p.ny / SPREAD_YB + 1) * 4;
-  const double per_probe = nq * 8 + plane * 8 + (double)F * g->nsel * 8 + spectrum_bytes_per_probe(g, F, precision,
-                                                                                                    reduce);
+  const double per_probe = nq * 8 + plane * 8 + (double)F * g->nsel * 8 +
+                           R * spectrum_bytes_per_probe(g, Fr, precision, reduce);
   const double cap = (double)run_cap(ctx);
   double room = cap - fixed - 2.0 * (double)kChunkCap;
   int64_t pb = room > per_probe ? (int64_t)(room / per_probe) : 1;
@@ -883,9 +942,10 @@ RunPlan run_plan(const tacaw_ctx* ctx, const tacaw_params& p, const GeoCache* g,
 
 // Device bytes a run allocates from the stream-ordered pool (tables cached in the context
 // are not counted), mirroring run_impl; used to admit serving requests.
-uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
-                       int32_t reduce, GeoCache* g) {
-  const RunPlan pl = run_plan(ctx, p, g, P, F, A, precision, reduce);
+uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t Fr, int64_t A, int32_t precision,
+                       int32_t reduce, GeoCache* g, int R) {
+  const RunPlan pl = run_plan(ctx, p, g, P, Fr, A, precision, reduce, R);
+  const int64_t F = Fr * R;
   const double nq = (double)p.nx * p.ny, plane = (double)p.ny * g->band.Wp, S = p.n_slices;
   const double chunk = (double)pl.rt.chunk, sb = pl.rt.sb, Pb = pl.Pb;
   const double tsz = (pl.tf ? plane : nq) * 8;
@@ -898,22 +958,27 @@ uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, 
   b += chunk * Pb * plane * 16;                                         // Apsi, Bpsi
   b += Pb * (nq * 8 + plane * 8);                                       // probes (and their column pass)
   b += Pb * (double)F * g->nsel * 8;                                    // compact exit waves
-  b += Pb * spectrum_bytes_per_probe(g, F, precision, reduce);
+  b += Pb * R * spectrum_bytes_per_probe(g, Fr, precision, reduce);
   return (uint64_t)(b * 1.05) + ((uint64_t)64 << 20);
 }
 
-// The whole path on device buffers, stream-ordered: positions d_pos [F][A][3] (device), Z
-// (host or device), S into d_S (device).  Scratch comes from the stream-ordered pool.  Probes
-// run in blocks (RunPlan): each block's waves are propagated through every frame, their
-// compact exit-wave stack is transformed, and the block's scratch is released before the next.
+// The whole path on device buffers, stream-ordered: positions d_pos [R Fr][A][3] (device: R
+// trajectories of Fr frames, one after the other), Z (host or device), S into d_S (device,
+// [P][R][Fr][ny][nx] or [P][R][Fr]).  Scratch comes from the stream-ordered pool.  Probes run
+// in blocks (RunPlan): each block's waves are propagated through every frame, their compact
+// exit-wave stack is transformed (one transform of Fr frames per probe and trajectory: the
+// stack [Pb][R Fr][n_sel] is [Pb R][Fr][n_sel]), and the block's scratch is released before
+// the next.
 int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const float* d_pos, const int32_t* Z,
-             bool z_dev, int64_t A, int64_t F, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st) {
+             bool z_dev, int64_t A, int64_t Fr, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st,
+             int R) {
+  const int64_t F = Fr * R;
   GeoCache* g;
   TRY_RC(get_geo(ctx, p, &g));
   Scratch sc(st);
   const int P = pr.n_probes, S = p.n_slices;
   const size_t nq = (size_t)p.nx * p.ny, plane = (size_t)p.ny * g->band.Wp;
-  const RunPlan pl = run_plan(ctx, p, g, P, F, A, precision, reduce);
+  const RunPlan pl = run_plan(ctx, p, g, P, Fr, A, precision, reduce, R);
   const RunTiling rt = pl.rt;
   const size_t tsz = pl.tf ? plane : nq;
   int8_t* slots;
@@ -965,7 +1030,7 @@ int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const
     }
     NvtxRange r("time_dft");
     float* out = d_S + (reduce == TACAW_REDUCE_NONE ? (size_t)p0 * F * nq : (size_t)p0 * F);
-    TRY_RC(spectrum_impl(ctx, psi_k, Pbc, F, io, precision, reduce, out, bsc));
+    TRY_RC(spectrum_impl(ctx, psi_k, (int64_t)Pbc * R, Fr, io, precision, reduce, out, bsc));
   }
   return TACAW_OK;
 }
@@ -1130,7 +1195,7 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   const size_t out_elems = reduce == TACAW_REDUCE_NONE ? (size_t)pr.n_probes * F * nq : (size_t)pr.n_probes * F;
   float* d_S = S_out;
   if (!out_dev) CK(sc.get(&d_S, out_elems));
-  TRY_RC(run_impl(ctx, p, pr, d_pos, Z, z_dev, A, F, precision, reduce, d_S, st));
+  TRY_RC(run_impl(ctx, p, pr, d_pos, Z, z_dev, A, F, precision, reduce, d_S, st, 1));
   if (!out_dev) {
     CK(cudaMemcpyAsync(S_out, d_S, sizeof(float) * out_elems, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1178,6 +1243,11 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (std::strcmp(name, "max_run_bytes") == 0) {
     if (value < 0) return set_err(ctx, TACAW_EINVAL, "max_run_bytes must be >= 0");
     ctx->max_run_bytes = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "max_coalesce") == 0) {
+    if (value < 1 || value > 1024) return set_err(ctx, TACAW_EINVAL, "max_coalesce must be in [1, 1024]");
+    ctx->max_coalesce = value;
     return TACAW_OK;
   }
   if (std::strcmp(name, "max_probe_block") == 0) {

@@ -556,6 +556,7 @@ int get_dft_operands(tacaw_ctx* ctx, int64_t F, bool tf32, int64_t kpad, void** 
   if (e == cudaSuccess) e = cudaMalloc(&dl, l.size());
   if (e == cudaSuccess) e = cudaMemcpy(dh, h.data(), h.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dl, l.data(), l.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);  // landed before any stream reads it
   if (e != cudaSuccess) {
     if (dh) cudaFree(dh);
     if (dl) cudaFree(dl);

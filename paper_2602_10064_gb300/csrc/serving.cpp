@@ -8,6 +8,15 @@
 // (continuous batching).  A request that does not fit may be overtaken by later ones that do,
 // at most kMaxSkips times; after that nothing is admitted ahead of it.  Per-request host
 // timestamps (submission, admission, completion) give latency percentiles.
+//
+// Requests of the same geometry (parameters, probes, frame and atom counts, species, arithmetic
+// and output) that are queued together are coalesced, up to the context option "max_coalesce"
+// (default 16), into one run: their
+// trajectories are stacked along the frame axis, so every slice launch, potential launch and
+// time-transform launch covers all of them, and each request's output is copied out of the
+// stacked result.  A coalesced request's result is the same, bit for bit, as alone: frames and
+// trajectories are independent in every kernel, and the launch grouping does not change the
+// arithmetic.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -56,6 +65,8 @@ struct Job {
   cudaEvent_t done = nullptr;
   float* d_pos_tmp = nullptr;
   float* d_S_tmp = nullptr;
+  std::vector<std::shared_ptr<Job>> followers;  // coalesced into this request's run
+  int batched = 1;                               // requests in the run this request is part of
   int status = TACAW_PENDING;
   bool canceled = false;
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -67,6 +78,7 @@ struct Serving {
   std::condition_variable cv, cv_done;
   std::thread worker;
   bool stop = false;
+  bool kick = false;  // set by submissions and shutdown: the queue changed
   std::deque<std::shared_ptr<Job>> queue;
   std::vector<std::shared_ptr<Job>> active;
   std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
@@ -87,8 +99,62 @@ void release(Serving& sv, Job& j) {
   j.stream = nullptr;
 }
 
+// Requests whose runs can be stacked along the frame axis: same geometry, beam, probes,
+// frame and atom counts, species, arithmetic and output.
+bool same_geometry(const Job& a, const Job& b) {
+  return std::memcmp(&a.params, &b.params, sizeof(tacaw_params)) == 0 && a.A == b.A && a.F == b.F &&
+         a.precision == b.precision && a.reduce == b.reduce && a.probe.alpha_mrad == b.probe.alpha_mrad &&
+         a.probe.n_probes == b.probe.n_probes && a.probe.defocus == b.probe.defocus &&
+         a.probe.cs_mm == b.probe.cs_mm && a.probe.astig == b.probe.astig &&
+         a.probe.astig_angle == b.probe.astig_angle && a.probe.psi0 == b.probe.psi0 && a.probe_xy == b.probe_xy &&
+         a.Z == b.Z;
+}
+
+// Enqueue a run of the leader j and its followers, trajectories stacked along the frame axis
+// (no serving lock held): positions gathered into one buffer, one run, each request's output
+// [P][F][..] copied out of the stacked [P][R][F][..] result.
+int launch_batch(Serving& sv, Job& j) {
+  tacaw_ctx* ctx = sv.ctx;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  std::vector<Job*> all{&j};
+  for (auto& f : j.followers) all.push_back(f.get());
+  const int R = (int)all.size();
+  const size_t per_pos = (size_t)j.F * j.A * 3, per_out = j.out_elems / (size_t)j.probe.n_probes;
+  const int P = j.probe.n_probes;
+  float *d_pos = nullptr, *d_S = nullptr;
+  if (j.A > 0) {
+    e = cudaMallocAsync((void**)&d_pos, sizeof(float) * per_pos * R, j.stream);
+    for (int r = 0; r < R && e == cudaSuccess; ++r) {
+      const float* src = all[r]->pos_dev ? all[r]->pos_dev : all[r]->pos_pinned;
+      e = cudaMemcpyAsync(d_pos + per_pos * r, src, sizeof(float) * per_pos, cudaMemcpyDefault, j.stream);
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "coalesced positions");
+  }
+  e = cudaMallocAsync((void**)&d_S, sizeof(float) * j.out_elems * R, j.stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "coalesced output");
+  int rc = run_impl(ctx, j.params, j.probe, d_pos, j.Z.data(), false, j.A, j.F, j.precision, j.reduce, d_S, j.stream,
+                    R);
+  for (int r = 0; r < R && rc == TACAW_OK; ++r) {
+    float* dst = all[r]->S_host ? all[r]->S_pinned : all[r]->S_user;
+    e = cudaMemcpy2DAsync(dst, sizeof(float) * per_out, d_S + per_out * r, sizeof(float) * per_out * R,
+                          sizeof(float) * per_out, (size_t)P, cudaMemcpyDefault, j.stream);
+    if (e != cudaSuccess) rc = cuda_err(ctx, e, "coalesced output copy");
+  }
+  if (d_pos) cudaFreeAsync(d_pos, j.stream);
+  cudaFreeAsync(d_S, j.stream);
+  if (rc == TACAW_OK) {
+    e = cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(j.done, j.stream);
+    if (e != cudaSuccess) rc = cuda_err(ctx, e, "request completion event");
+  }
+  return rc;
+}
+
 // Enqueue one admitted request on its stream (no serving lock held).
 int launch(Serving& sv, Job& j) {
+  if (!j.followers.empty()) return launch_batch(sv, j);
   tacaw_ctx* ctx = sv.ctx;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -124,6 +190,8 @@ int launch(Serving& sv, Job& j) {
 }
 
 void finish(Serving& sv, Job& j, int status) {
+  for (auto& f : j.followers) finish(sv, *f, status);
+  j.followers.clear();
   if (status == TACAW_OK && j.S_host && !j.canceled) std::memcpy(j.S_user, j.S_pinned, sizeof(float) * j.out_elems);
   j.status = j.canceled ? TACAW_ECANCELED : status;
   j.t_done = now_s();
@@ -136,8 +204,14 @@ void worker_loop(Serving* svp) {
   cudaSetDevice(sv.ctx->device);
   std::unique_lock<std::mutex> lk(sv.mu);
   while (true) {
-    sv.cv.wait_for(lk, std::chrono::microseconds(200),
-                   [&] { return sv.stop || !sv.queue.empty() || !sv.active.empty(); });
+    // sleep with the lock released until the queue changes, polling the running requests'
+    // completions every 100 us (every 50 ms when nothing runs); a wait whose predicate held
+    // from the start would keep the lock, and submissions could not enqueue while any
+    // request ran
+    const bool busy = !sv.active.empty() || !sv.queue.empty();
+    sv.cv.wait_for(lk, busy ? std::chrono::microseconds(100) : std::chrono::microseconds(50000),
+                   [&] { return sv.stop || sv.kick; });
+    sv.kick = false;
     // completions
     for (size_t i = 0; i < sv.active.size();) {
       Job& j = *sv.active[i];
@@ -169,6 +243,22 @@ void worker_loop(Serving* svp) {
       sv.free_streams.pop_back();
       sv.used += j.footprint;
       j.t_admit = now_s();
+      // coalesce queued requests of the same geometry that also fit (each reserves its own
+      // footprint, an upper bound of its share of the stacked run)
+      const int64_t max_batch = sv.ctx->max_coalesce;
+      for (auto k = sv.queue.begin(); k != sv.queue.end() && (int64_t)j.followers.size() + 1 < max_batch;) {
+        Job& c = **k;
+        if (same_geometry(j, c) && sv.used + c.footprint <= sv.ctx->budget) {
+          sv.used += c.footprint;
+          c.t_admit = j.t_admit;
+          j.followers.push_back(*k);
+          k = sv.queue.erase(k);
+        } else {
+          ++k;
+        }
+      }
+      j.batched = 1 + (int)j.followers.size();
+      for (auto& f : j.followers) f->batched = j.batched;
       lk.unlock();
       const int rc = launch(sv, j);
       lk.lock();
@@ -219,7 +309,7 @@ Serving* serving_of(tacaw_ctx* ctx, int* rc) {
 void fill(const Job& j, tacaw_result* out) {
   if (!out) return;
   out->status = j.status;
-  out->pad_ = 0;
+  out->batched = j.batched;
   out->footprint_bytes = j.footprint;
   out->t_submit = j.t_submit;
   out->t_admit = j.t_admit;
@@ -234,6 +324,7 @@ void serving_shutdown(tacaw_ctx* ctx) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stop = true;
+    sv->kick = true;
   }
   sv->cv.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
@@ -342,6 +433,7 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
     j->t_submit = now_s();
     sv->jobs[j->ticket] = j;
     sv->queue.push_back(j);
+    sv->kick = true;
     *ticket = j->ticket;
   }
   sv->cv.notify_all();

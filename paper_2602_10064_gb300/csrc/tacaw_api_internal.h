@@ -59,8 +59,24 @@ struct Profiler {
   std::vector<std::string> select;  // classes timed with events; empty: every class
 };
 
+// Pinned staging for the small host tables a run uploads (species slots, probe phase tables):
+// a copy from pageable memory first waits for the stream's earlier work, which would make the
+// launching thread wait for the GPU; from this ring the copy is asynchronous.  A region is
+// reused only after the event recorded behind its copy has completed.
+struct PinnedRing {
+  unsigned char* base = nullptr;
+  size_t cap = 0, head = 0;
+  struct Span {
+    size_t off, end;
+    cudaEvent_t done;
+  };
+  std::vector<Span> inflight;          // in allocation order
+  std::vector<cudaEvent_t> free_events;
+};
+
 struct tacaw_ctx {
   Profiler prof;
+  PinnedRing staging;
   int device = 0;
   uint64_t budget = 0;
   std::string err;
@@ -79,6 +95,7 @@ struct tacaw_ctx {
   int64_t min_wave_rows = 0;     // option: wave rows a slice launch should hold (0 = default)
   int64_t max_run_bytes = 0;     // option: scratch bound of one run (0 = automatic)
   int64_t max_probe_block = 0;   // option: cap on the probes propagated and transformed together
+  int64_t max_coalesce = 16;     // option: serving requests of one geometry coalesced into a run
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };
@@ -128,6 +145,11 @@ struct SpecIO {
   const int32_t* out_qsel;
 };
 
+// Host -> device copy of `bytes` from pageable src through the context's pinned ring
+// (asynchronous on st: src may be reused as soon as this returns).  Larger than the ring:
+// a plain copy from pageable memory.
+cudaError_t staged_copy(tacaw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 int set_err(tacaw_ctx* c, int code, const char* fmt, ...);
 int cuda_err(tacaw_ctx* c, cudaError_t e, const char* where);
 int get_time_tw(tacaw_ctx* ctx, int64_t F, float2** out);
@@ -145,10 +167,13 @@ int get_geo(tacaw_ctx* ctx, const tacaw_params& p, GeoCache** out);
 int check_run(tacaw_ctx* ctx, const tacaw_params* params, const tacaw_probe& pr, const float* pos,
               const int32_t* Z, int64_t n_atoms, int64_t n_frames, int32_t precision, int32_t reduce,
               const float* S_out, bool buffers);
+// R trajectories of F frames each stacked along the frame axis run as one (shared launches);
+// the output is [P][R][F][ny][nx] or [P][R][F].
 uint64_t run_footprint(tacaw_ctx* ctx, const tacaw_params& p, int P, int64_t F, int64_t A, int32_t precision,
-                       int32_t reduce, GeoCache* g);
+                       int32_t reduce, GeoCache* g, int R = 1);
 int run_impl(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, const float* d_pos, const int32_t* Z,
-             bool z_dev, int64_t A, int64_t F, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st);
+             bool z_dev, int64_t A, int64_t F, int32_t precision, int32_t reduce, float* d_S, cudaStream_t st,
+             int R = 1);
 // serving loop (serving.cpp)
 void serving_shutdown(tacaw_ctx* ctx);
 

@@ -48,17 +48,19 @@ def run_alone(T, ctx, w, precision):
                    precision=precision).cpu().numpy()
 
 
-def submit(T, ctx, w, precision, host=False):
+def submit(T, ctx, w, precision, host=False, reduce=None):
     import torch
     P = w.n_probes
+    reduce = T.REDUCE_NONE if reduce is None else reduce
+    shape = (P, w.n_frames, w.ny, w.nx) if reduce == T.REDUCE_NONE else (P, w.n_frames)
     if host:
         pos, Z = w.pos, w.Z
-        out = np.zeros((P, w.n_frames, w.ny, w.nx), np.float32)
+        out = np.zeros(shape, np.float32)
     else:
         pos, Z = torch.from_numpy(w.pos).cuda(), torch.from_numpy(w.Z).cuda()
-        out = torch.zeros((P, w.n_frames, w.ny, w.nx), dtype=torch.float32, device="cuda")
+        out = torch.zeros(shape, dtype=torch.float32, device="cuda")
     pr = T.probe_of(w)
-    req = T.make_request(T.params_of(w), pos, Z, w.n_atoms, w.n_frames, pr, precision, T.REDUCE_NONE, out)
+    req = T.make_request(T.params_of(w), pos, Z, w.n_atoms, w.n_frames, pr, precision, reduce, out)
     t = T.tacaw_submit(ctx.h, req)
     return t, out, (pos, Z, pr)
 
@@ -152,3 +154,42 @@ def test_cancel_queued_request(T):
         assert all(c == T.TACAW_OK for c in codes[:-1])
         assert codes[-1] in (T.TACAW_ECANCELED, T.TACAW_OK)
         assert T.tacaw_poll(ctx.h, last)[0] == T.TACAW_ENOTFOUND
+
+
+@pytest.mark.parametrize("scan", [False, True])
+def test_same_geometry_requests_share_a_run(T, scan):
+    """Queued requests of one geometry (different trajectories) are coalesced into one run whose
+    launches cover all of them; each result equals the request run alone, bit for bit."""
+    import torch
+    ws = []
+    for k in range(6):
+        w = workloads.diamond_si(n_frames=16, grid=64, n_slices=4, seed=90 + k)
+        if scan:
+            w.alpha_mrad, w.probes = 30.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
+        ws.append(w)
+    # (of different frame counts: requests of one geometry would be coalesced into one run)
+    blockers = [workloads.config2(n_frames=160 + 16 * k, seed=97 + k) for k in range(4)]
+    fz, fc = table_for(ws + blockers)
+    reduce = T.REDUCE_DETECTOR if scan else T.REDUCE_NONE
+    with T.Context(0) as ctx:
+        ctx.load_form_factors(fz, fc)
+        alone = []
+        for w in ws:
+            S = ctx.run(T.params_of(w), torch.from_numpy(w.pos).cuda(), torch.from_numpy(w.Z).cuda(),
+                        T.probe_of(w), precision=T.DFT_BF16X3, reduce=reduce).cpu().numpy()
+            alone.append(S)
+        torch.cuda.synchronize()
+        # four longer requests occupy the serving streams, so the six queue up together
+        busy = [submit(T, ctx, w, T.DFT_BF16X3) for w in blockers]
+        subs = [submit(T, ctx, w, T.DFT_BF16X3, host=(i % 3 == 2), reduce=reduce) for i, w in enumerate(ws)]
+        batched = []
+        for (t, out, keep), ref in zip(subs, alone):
+            rc, r = T.tacaw_wait(ctx.h, t, 300.0)
+            assert rc == T.TACAW_OK, rc
+            got = out.cpu().numpy() if hasattr(out, "cpu") else out
+            assert np.array_equal(got, ref)
+            batched.append(r.batched)
+        for t, out, keep in busy:
+            assert T.tacaw_wait(ctx.h, t, 300.0)[0] == T.TACAW_OK
+        ctx.check()
+    assert max(batched) > 1, batched

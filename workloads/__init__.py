@@ -323,20 +323,28 @@ class RequestSpec:
 
 def request_stream(n_requests=200, seed=5, rate_hz=10.0, grids=(128, 256, 512, 1024),
                    frames=(64, 128, 256, 512, 1024), slices=(8, 40), reps=(2, 13), scans=(4, 16),
-                   p_plane=0.5):
-    """Poisson arrivals of random cubic-cell requests (diamond Si or rocksalt Mg/O)."""
+                   p_plane=0.5, n_geometries=None):
+    """Poisson arrivals of random cubic-cell requests (diamond Si or rocksalt Mg/O).  With
+    n_geometries, every request takes one of that many seeded geometries (crystal, size, grid,
+    frames, slices, probes) and its own trajectory seed: repeated screening of a few systems."""
     rng = SplitMix64(seed)
-    t = 0.0
-    out = []
-    for i in range(n_requests):
-        t += -math.log(1.0 - rng.uniform()) / rate_hz
+
+    def geometry():
         crystal = "diamond" if rng.uniform() < 0.5 else "rocksalt"
         r = rng.randint(reps[0], reps[1])
         g = grids[rng.randint(0, len(grids) - 1)]
         F = frames[rng.randint(0, len(frames) - 1)]
         S = rng.randint(slices[0], slices[1])
         scan = 0 if rng.uniform() < p_plane else rng.randint(scans[0], scans[1])
-        out.append(RequestSpec(i, t, crystal, r, g, F, S, scan, rng.next_u64() & 0xFFFFFFFF))
+        return crystal, r, g, F, S, scan
+
+    pool = [geometry() for _ in range(n_geometries)] if n_geometries else None
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += -math.log(1.0 - rng.uniform()) / rate_hz
+        geo = pool[rng.randint(0, len(pool) - 1)] if pool else geometry()
+        out.append(RequestSpec(i, t, *geo, rng.next_u64() & 0xFFFFFFFF))
     return out
 
 
