@@ -320,7 +320,7 @@ FULL_MIX = dict(grids=(128, 256, 512, 1024), frames=(64, 128, 256, 512, 1024), s
 
 
 def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm=True, plain_sample=None,
-                n_geometries=None):
+                n_geometries=None, streams=None):
     """Serve n_requests seeded requests arriving as a Poisson stream at rate_factor x the
     measured batched capacity; compare with the plain path (requests one by one).  Plane-wave
     requests return the full S, probe scans the detector-summed spectrum image.
@@ -346,6 +346,8 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm
     # the context after the request buffers: its serving budget is 90% of the memory left
     ctx = T.Context(device)
     ctx.load_form_factors(fz, fc)
+    if streams:
+        ctx.set_option("serving_streams", streams)
     work = lambda r: r["w"].n_probes * r["w"].n_frames * r["w"].n_slices
     pxwork = lambda r: work(r) * r["w"].nx * r["w"].ny
     units = sum(work(r) for r in reqs)
@@ -435,6 +437,7 @@ def run_serving(T, n_requests, seed=5, rate_factor=0.8, device=0, mix=None, warm
         "precision": "bf16x3 served, fp32 plain (both within 1e-4 of the oracle in the tests)",
         "warmed": warm,
         "coalesced_requests": coalesced, "mean_run_size": float(np.mean(batch)) if batch else 1.0,
+        "serving_streams": streams or 4,
         **({"geometries": n_geometries,
             "capacity_without_coalescing_spectra_per_s": spectra / cap_nocoal_s,
             "coalescing_speedup": cap_nocoal_s / cap_s} if n_geometries else {}),
@@ -462,6 +465,7 @@ def main():
     ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
                     help="context option (tacaw_set_option) for the timed runs, e.g. max_chunk_frames=2")
     ap.add_argument("--serving-requests", type=int, default=24, help="requests in the serving run (0: skip)")
+    ap.add_argument("--serving-streams", type=int, default=0, help="c5: serving streams (0: the library default)")
     ap.add_argument("--serving-mix", default="full", choices=["full", "small"],
                     help="c5: the configuration's full request ranges, or the small mix of the default line")
     ap.add_argument("--serving-geometries", type=int, default=0,
@@ -625,7 +629,8 @@ def main_serving(args, rank, world, local):
     clocks.start()
     mix = FULL_MIX if args.serving_mix == "full" else SERVING_MIX
     r = run_serving(T, n, seed=5 + 1000 * rank, device=local, mix=mix, warm=False,
-                    plain_sample=args.plain_sample or None, n_geometries=args.serving_geometries or None)
+                    plain_sample=args.plain_sample or None, n_geometries=args.serving_geometries or None,
+                    streams=args.serving_streams or None)
     clk = clocks.stop()
     if rank != 0:
         return

@@ -250,7 +250,8 @@ typedef struct tacaw_result {
 
 /* Queue a request (non-blocking).  The request is checked now (EINVAL as tacaw_run; ETOOBIG if
  * its footprint exceeds the context's budget).  A worker thread admits queued requests while
- * their footprints fit the budget and one of the context's serving streams is free, and runs
+ * their footprints fit the budget and one of the context's serving streams (option
+ * "serving_streams") is free, and runs
  * each on its own stream, so admitted requests overlap on the GPU; later requests are admitted
  * as memory frees up.  A request that does not fit can be overtaken by smaller ones at most 8
  * times.  Queued requests of the same geometry (parameters, probes, frame and atom counts,
@@ -318,6 +319,8 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * context's budget, at most 64 GiB); probes are propagated and transformed in blocks sized to
  * it.  "max_probe_block": cap on the probes of one block (0 = no cap).  "max_coalesce": the most
  * queued serving requests of one geometry coalesced into one run (default 16; 1 = none).
+ * "serving_streams": streams on which admitted serving requests run concurrently (default 4;
+ * before the first tacaw_submit only).
  * Results do not depend on these options.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 

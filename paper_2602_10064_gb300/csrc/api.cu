@@ -1245,6 +1245,12 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
     ctx->max_run_bytes = value;
     return TACAW_OK;
   }
+  if (std::strcmp(name, "serving_streams") == 0) {
+    if (value < 1 || value > 64) return set_err(ctx, TACAW_EINVAL, "serving_streams must be in [1, 64]");
+    if (ctx->serving) return set_err(ctx, TACAW_EINVAL, "serving_streams must be set before the first tacaw_submit");
+    ctx->serving_streams = value;
+    return TACAW_OK;
+  }
   if (std::strcmp(name, "max_coalesce") == 0) {
     if (value < 1 || value > 1024) return set_err(ctx, TACAW_EINVAL, "max_coalesce must be in [1, 1024]");
     ctx->max_coalesce = value;

@@ -317,15 +317,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       } else {
-        // detector sum: |psi~|^2 rounded to float as a stored S would be, summed in FP64 over
-        // this thread's columns, then over the two column halves in a fixed order
-        double dsum = 0.0;
+        // detector sum: |psi~|^2 rounded to float as a stored S would be, summed over this
+        // thread's columns as an FP32 pair (error-free two-sums: FP64-class, since GB300's FP64
+        // pipe would take longer than the tile's MMAs), the pair combined in FP64, then the two
+        // column halves added in FP64 in a fixed order
+        float dh = 0.f, dl = 0.f;
 #pragma unroll
         for (int i = 0; i < TC_EPI_COLS; ++i) {
           const float o = __shfl_xor_sync(0xffffffffu, acc[i], 1);
           const float sv = acc[i] * acc[i] + o * o;
-          if (j0 + i < nsel) dsum += (double)sv;
+          if (j0 + i < nsel) pair_add(dh, dl, sv);
         }
+        const double dsum = (double)dh + (double)dl;
         const int r = (32 * quarter + lane) >> 1;
         if ((lane & 1) == 0) red[half * (TC_BM / 2) + r] = dsum;
         // every epilogue warp arrives here for every tile, also after a timed-out wait
@@ -356,8 +359,9 @@ __device__ __forceinline__ float to_tf32(float x) {
 // the FP32 path), then the CTA walks the frames in 32 x 32 (j, n) tiles, transposed through
 // shared memory; the second read of the column block comes from L2.  The difference is formed
 // exactly as the FP32 pair (r, re) (pair_sub: the FP64 mean as an FP32 pair); hi = r rounded to
-// the operand type, lo = (r - hi) + re, where r - hi is exact.
-constexpr int RS_GROUPS = 8;
+// the operand type, lo = (r - hi) + re, where r - hi is exact.  A tile holds RS_TN frames, so
+// each thread has RS_TN / 8 loads in flight between two barriers.
+constexpr int RS_GROUPS = 8, RS_TN = 64;
 template <bool TF32>
 __global__ void __launch_bounds__(256) k_mean_residual_split(const float2* __restrict__ psi, int64_t F, int64_t nq,
                                                              const int32_t* __restrict__ qsel, int64_t nsel,
@@ -365,7 +369,7 @@ __global__ void __launch_bounds__(256) k_mean_residual_split(const float2* __res
                                                              void* __restrict__ Blo) {
   __shared__ float4 part[RS_GROUPS][32];
   __shared__ float4 msplit[32];  // mean as FP32 pairs (hi.x, lo.x, hi.y, lo.y)
-  __shared__ float2 hs[32][33], ls[32][33];
+  __shared__ float2 hs[RS_TN][33], ls[RS_TN][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t J0 = (int64_t)blockIdx.x * 32;
   // columns j >= nsel of a probe (padding) are zero; a block of 32 lies inside one probe
@@ -387,9 +391,10 @@ __global__ void __launch_bounds__(256) k_mean_residual_split(const float2* __res
   }
   __syncthreads();
   const float4 m = msplit[tx];
-  for (int64_t n0 = 0; 2 * n0 < kpad2; n0 += 32) {
+  for (int64_t n0 = 0; 2 * n0 < kpad2; n0 += RS_TN) {
     // phase 1: coalesced along j
-    for (int r = ty; r < 32; r += 8) {
+#pragma unroll
+    for (int r = ty; r < RS_TN; r += 8) {
       const int64_t n = n0 + r;
       float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
       if (live && n < F) {
@@ -411,11 +416,12 @@ __global__ void __launch_bounds__(256) k_mean_residual_split(const float2* __res
     }
     __syncthreads();
     // phase 2: each warp writes rows J (contiguous along n)
-    for (int c = ty; c < 32; c += 8) {
+    for (int cr = ty; cr < 32 * (RS_TN / 32); cr += 8) {
+      const int c = cr & 31, h0 = (cr >> 5) * 32;
       const int64_t Jw = J0 + c;
-      const int64_t n = n0 + tx;
+      const int64_t n = n0 + h0 + tx;
       if (2 * n >= kpad2) continue;
-      const float2 h = hs[tx][c], l = ls[tx][c];
+      const float2 h = hs[h0 + tx][c], l = ls[h0 + tx][c];
       if (TF32) {
         reinterpret_cast<float2*>(Bhi)[(size_t)Jw * (kpad2 / 2) + n] = h;
         reinterpret_cast<float2*>(Blo)[(size_t)Jw * (kpad2 / 2) + n] = l;

@@ -35,7 +35,6 @@
 namespace tacaw {
 
 namespace {
-constexpr int kStreams = 4;
 constexpr int kMaxSkips = 8;
 
 double now_s() {
@@ -290,7 +289,7 @@ Serving* serving_of(tacaw_ctx* ctx, int* rc) {
   auto* sv = new Serving();
   sv->ctx = ctx;
   cudaSetDevice(ctx->device);
-  for (int i = 0; i < kStreams; ++i) {
+  for (int64_t i = 0; i < ctx->serving_streams; ++i) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       *rc = set_err(ctx, TACAW_ECUDA, "cannot create serving streams");

@@ -96,6 +96,7 @@ struct tacaw_ctx {
   int64_t max_run_bytes = 0;     // option: scratch bound of one run (0 = automatic)
   int64_t max_probe_block = 0;   // option: cap on the probes propagated and transformed together
   int64_t max_coalesce = 16;     // option: serving requests of one geometry coalesced into a run
+  int64_t serving_streams = 4;   // option: streams of the serving loop (set before the first submit)
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };
