@@ -282,6 +282,14 @@ int tacaw_wait(tacaw_ctx* ctx, uint64_t ticket, double timeout_s, tacaw_result* 
  * the end but reports TACAW_ECANCELED (its host output is not written). */
 int tacaw_cancel(tacaw_ctx* ctx, uint64_t ticket);
 
+/* Hold (hold != 0) or release (0) admission: while held, submitted requests queue and none is
+ * admitted (running ones continue).  Releasing admits the queue at once, and queued requests of
+ * one geometry are coalesced into shared runs (up to the option "max_coalesce"), so a caller
+ * that submits a batch between hold and release gets the batch's runs stacked.  Requests still
+ * queued when the context is destroyed finish with TACAW_ECANCELED.  TACAW_EINVAL for a null
+ * context. */
+int tacaw_serving_hold(tacaw_ctx* ctx, int32_t hold);
+
 /* Current serving load: queued and running requests, reserved and budgeted device bytes. */
 int tacaw_serving_stats(tacaw_ctx* ctx, int64_t* queued, int64_t* active, uint64_t* used_bytes,
                         uint64_t* budget_bytes);
@@ -319,8 +327,11 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * context's budget, at most 64 GiB); probes are propagated and transformed in blocks sized to
  * it.  "max_probe_block": cap on the probes of one block (0 = no cap).  "max_coalesce": the most
  * queued serving requests of one geometry coalesced into one run (default 16; 1 = none).
- * "serving_streams": streams on which admitted serving requests run concurrently (default 4;
- * before the first tacaw_submit only).
+ * "serving_streams": streams per request class on which admitted serving requests run
+ * concurrently (default 4; before the first tacaw_submit only).  "serving_small_work": requests
+ * whose work (probes x frames x slices x nx x ny) is at most this (default 2^33) run on
+ * high-priority streams of their own, so they wait neither for long requests' streams nor for
+ * their pending blocks; the others on normal-priority streams.
  * Results do not depend on these options.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 

@@ -144,6 +144,7 @@ def lib():
             "tacaw_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result)]),
             "tacaw_wait": (C.c_int, [vp, C.c_uint64, C.c_double, C.POINTER(Result)]),
             "tacaw_cancel": (C.c_int, [vp, C.c_uint64]),
+            "tacaw_serving_hold": (C.c_int, [vp, C.c_int32]),
             "tacaw_serving_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_uint64),
                                               C.POINTER(C.c_uint64)]),
             "tacaw_profile_begin": (C.c_int, [vp]),
@@ -158,10 +159,11 @@ def lib():
 
 
 def exported_symbols():
-    return ["tacaw_version", "tacaw_axes", "tacaw_create", "tacaw_destroy", "tacaw_last_error", "tacaw_load_form_factors",
-            "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission", "tacaw_propagate",
-            "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin", "tacaw_profile_select", "tacaw_profile_end",
-            "tacaw_spectrum_static", "tacaw_submit", "tacaw_request_footprint", "tacaw_poll", "tacaw_wait", "tacaw_cancel",
+    return ["tacaw_version", "tacaw_axes", "tacaw_create", "tacaw_destroy", "tacaw_last_error",
+            "tacaw_load_form_factors", "tacaw_bin_slices", "tacaw_build_potential", "tacaw_transmission",
+            "tacaw_propagate", "tacaw_spectrum", "tacaw_run", "tacaw_check", "tacaw_profile_begin",
+            "tacaw_profile_select", "tacaw_profile_end", "tacaw_spectrum_static", "tacaw_submit",
+            "tacaw_request_footprint", "tacaw_poll", "tacaw_wait", "tacaw_cancel", "tacaw_serving_hold",
             "tacaw_serving_stats", "tacaw_set_option", "tacaw_spectral_diffraction", "tacaw_dispersion",
             "tacaw_accumulate", "tacaw_selftest_wait", "tacaw_band_points", "tacaw_spectrum_partial",
             "tacaw_intensity"]
@@ -291,6 +293,11 @@ def tacaw_wait(ctx, ticket, timeout_s=-1.0):
 
 def tacaw_cancel(ctx, ticket):
     return lib().tacaw_cancel(ctx, ticket)
+
+
+def tacaw_serving_hold(ctx, hold):
+    """Hold (True) or release (False) admission of queued requests; see include/tacaw.h."""
+    _check(ctx, lib().tacaw_serving_hold(ctx, 1 if hold else 0))
 
 
 def tacaw_serving_stats(ctx):

@@ -225,7 +225,10 @@ namespace {
 template <class T>
 int owned_alloc(tacaw_ctx* ctx, T** p, size_t n) {
   void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, sizeof(T) * std::max<size_t>(n, 1));
+  // stream-ordered on the legacy stream (which non-blocking streams do not wait for): a plain
+  // cudaMalloc can wait for the whole device, and tables are built while requests run; the
+  // builders synchronise the legacy stream before the tables are used
+  cudaError_t e = cudaMallocAsync(&v, sizeof(T) * std::max<size_t>(n, 1), 0);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMalloc");
   ctx->owned.push_back(v);
   *p = static_cast<T*>(v);
@@ -1249,6 +1252,11 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
     if (value < 1 || value > 64) return set_err(ctx, TACAW_EINVAL, "serving_streams must be in [1, 64]");
     if (ctx->serving) return set_err(ctx, TACAW_EINVAL, "serving_streams must be set before the first tacaw_submit");
     ctx->serving_streams = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "serving_small_work") == 0) {
+    if (value < 0) return set_err(ctx, TACAW_EINVAL, "serving_small_work must be >= 0");
+    ctx->serving_small_work = value;
     return TACAW_OK;
   }
   if (std::strcmp(name, "max_coalesce") == 0) {

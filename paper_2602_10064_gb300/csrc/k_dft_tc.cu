@@ -558,8 +558,9 @@ int get_dft_operands(tacaw_ctx* ctx, int64_t F, bool tf32, int64_t kpad, void** 
       }
     }
   void *dh = nullptr, *dl = nullptr;
-  cudaError_t e = cudaMalloc(&dh, h.size());
-  if (e == cudaSuccess) e = cudaMalloc(&dl, l.size());
+  // stream-ordered on the legacy stream, which requests on non-blocking streams do not wait for
+  cudaError_t e = cudaMallocAsync(&dh, h.size(), 0);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dl, l.size(), 0);
   if (e == cudaSuccess) e = cudaMemcpy(dh, h.data(), h.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dl, l.data(), l.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamSynchronize(0);  // landed before any stream reads it

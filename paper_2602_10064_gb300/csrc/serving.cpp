@@ -9,8 +9,14 @@
 // at most kMaxSkips times; after that nothing is admitted ahead of it.  Per-request host
 // timestamps (submission, admission, completion) give latency percentiles.
 //
+// Requests come in two classes by their work (probes x frames x slices x grid points): small
+// ones run on high-priority streams of their own and large ones on normal-priority streams, so
+// a small request neither waits for a stream held by a long scan nor, once launched, for the
+// long scan's pending blocks.  Each class has "serving_streams" streams.
+//
 // Requests of the same geometry (parameters, probes, frame and atom counts, species, arithmetic
-// and output) that are queued together are coalesced, up to the context option "max_coalesce"
+// and output) that are queued together are coalesced (tacaw_serving_hold queues a batch of
+// requests before any of them is admitted), up to the context option "max_coalesce"
 // (default 16), into one run: their
 // trajectories are stacked along the frame axis, so every slice launch, potential launch and
 // time-transform launch covers all of them, and each request's output is copied out of the
@@ -24,6 +30,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -36,6 +43,8 @@ namespace tacaw {
 
 namespace {
 constexpr int kMaxSkips = 8;
+constexpr size_t kPinnedMinBlock = (size_t)64 << 10;
+constexpr size_t kPinnedCacheBytes = (size_t)4 << 30;
 
 double now_s() {
   using namespace std::chrono;
@@ -65,23 +74,73 @@ struct Job {
   float* d_pos_tmp = nullptr;
   float* d_S_tmp = nullptr;
   std::vector<std::shared_ptr<Job>> followers;  // coalesced into this request's run
+  int cls = 0;                                   // stream class: 1 small (high priority), 0 large
   int batched = 1;                               // requests in the run this request is part of
   int status = TACAW_PENDING;
   bool canceled = false;
   double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
+// Page-locked host blocks for the requests' host inputs and outputs, reused across requests:
+// allocating or freeing page-locked memory can wait for the whole device, which would hold
+// a submission, or the worker finishing a request, behind every running request.  Blocks come
+// in power-of-two sizes from 64 KiB; at most kPinnedCacheBytes of free blocks are kept.
+struct PinnedPool {
+  std::mutex mu;
+  std::multimap<size_t, void*> free_blocks;  // block size -> block
+  std::unordered_map<void*, size_t> size_of;  // every block handed out or free
+  size_t cached = 0;
+
+  cudaError_t get(size_t bytes, void** p) {
+    size_t b = kPinnedMinBlock;
+    while (b < bytes) b <<= 1;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = free_blocks.find(b);
+    if (it != free_blocks.end()) {
+      *p = it->second;
+      free_blocks.erase(it);
+      cached -= b;
+      return cudaSuccess;
+    }
+    const cudaError_t e = cudaMallocHost(p, b);
+    if (e == cudaSuccess) size_of[*p] = b;
+    return e;
+  }
+  void put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = size_of.find(p);
+    if (it == size_of.end()) return;
+    if (cached + it->second > kPinnedCacheBytes) {
+      cudaFreeHost(p);
+      size_of.erase(it);
+      return;
+    }
+    free_blocks.emplace(it->second, p);
+    cached += it->second;
+  }
+  void clear() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& kv : size_of) cudaFreeHost(kv.first);
+    size_of.clear();
+    free_blocks.clear();
+    cached = 0;
+  }
+};
+
 struct Serving {
   tacaw_ctx* ctx = nullptr;
+  PinnedPool pinned;
   std::mutex mu;
   std::condition_variable cv, cv_done;
   std::thread worker;
   bool stop = false;
   bool kick = false;  // set by submissions and shutdown: the queue changed
+  bool hold = false;  // tacaw_serving_hold: nothing is admitted while set
   std::deque<std::shared_ptr<Job>> queue;
   std::vector<std::shared_ptr<Job>> active;
   std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
-  std::vector<cudaStream_t> free_streams;
+  std::vector<cudaStream_t> free_streams[2];  // per class: 0 large, 1 small (high priority)
   std::vector<cudaStream_t> all_streams;
   uint64_t next_ticket = 1, used = 0;
 };
@@ -89,12 +148,12 @@ struct Serving {
 namespace {
 
 void release(Serving& sv, Job& j) {
-  if (j.pos_pinned) cudaFreeHost(j.pos_pinned);
-  if (j.S_pinned) cudaFreeHost(j.S_pinned);
+  sv.pinned.put(j.pos_pinned);
+  sv.pinned.put(j.S_pinned);
   j.pos_pinned = j.S_pinned = nullptr;
   if (j.done) cudaEventDestroy(j.done);
   j.done = nullptr;
-  if (j.stream) sv.free_streams.push_back(j.stream);
+  if (j.stream) sv.free_streams[j.cls].push_back(j.stream);
   j.stream = nullptr;
 }
 
@@ -227,8 +286,13 @@ void worker_loop(Serving* svp) {
     // admissions: in order; one request that does not fit may be overtaken, at most
     // kMaxSkips times, after which nothing is admitted ahead of it
     Job* blocked = nullptr;
-    for (auto it = sv.queue.begin(); !sv.stop && it != sv.queue.end() && !sv.free_streams.empty();) {
+    for (auto it = sv.queue.begin();
+         !sv.stop && !sv.hold && it != sv.queue.end() && (!sv.free_streams[0].empty() || !sv.free_streams[1].empty());) {
       Job& j = **it;
+      if (sv.free_streams[j.cls].empty()) {  // its class's streams are all busy
+        ++it;
+        continue;
+      }
       if (sv.used + j.footprint > sv.ctx->budget) {
         if (blocked || j.skips >= kMaxSkips) break;
         blocked = &j;
@@ -238,8 +302,8 @@ void worker_loop(Serving* svp) {
       if (blocked) ++blocked->skips;
       std::shared_ptr<Job> jp = *it;
       it = sv.queue.erase(it);
-      j.stream = sv.free_streams.back();
-      sv.free_streams.pop_back();
+      j.stream = sv.free_streams[j.cls].back();
+      sv.free_streams[j.cls].pop_back();
       sv.used += j.footprint;
       j.t_admit = now_s();
       // coalesce queued requests of the same geometry that also fit (each reserves its own
@@ -275,8 +339,8 @@ void worker_loop(Serving* svp) {
   for (auto& jp : sv.queue) {
     jp->canceled = true;
     jp->status = TACAW_ECANCELED;
-    if (jp->pos_pinned) cudaFreeHost(jp->pos_pinned);
-    if (jp->S_pinned) cudaFreeHost(jp->S_pinned);
+    sv.pinned.put(jp->pos_pinned);
+    sv.pinned.put(jp->S_pinned);
     jp->pos_pinned = jp->S_pinned = nullptr;
   }
   sv.queue.clear();
@@ -289,17 +353,20 @@ Serving* serving_of(tacaw_ctx* ctx, int* rc) {
   auto* sv = new Serving();
   sv->ctx = ctx;
   cudaSetDevice(ctx->device);
-  for (int64_t i = 0; i < ctx->serving_streams; ++i) {
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      *rc = set_err(ctx, TACAW_ECUDA, "cannot create serving streams");
-      for (cudaStream_t t : sv->all_streams) cudaStreamDestroy(t);
-      delete sv;
-      return nullptr;
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  for (int cls = 0; cls < 2; ++cls)
+    for (int64_t i = 0; i < ctx->serving_streams; ++i) {
+      cudaStream_t s;
+      if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, cls ? greatest : least) != cudaSuccess) {
+        *rc = set_err(ctx, TACAW_ECUDA, "cannot create serving streams");
+        for (cudaStream_t t : sv->all_streams) cudaStreamDestroy(t);
+        delete sv;
+        return nullptr;
+      }
+      sv->all_streams.push_back(s);
+      sv->free_streams[cls].push_back(s);
     }
-    sv->all_streams.push_back(s);
-    sv->free_streams.push_back(s);
-  }
   sv->worker = std::thread(worker_loop, sv);
   ctx->serving = sv;
   return sv;
@@ -331,6 +398,7 @@ void serving_shutdown(tacaw_ctx* ctx) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   }
+  sv->pinned.clear();
   ctx->serving = nullptr;
   delete sv;
 }
@@ -344,6 +412,10 @@ extern "C" {
 int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
   if (!ctx || !req || !ticket) return TACAW_EINVAL;
   auto j = std::make_shared<Job>();
+  int rc = TACAW_OK;
+  Serving* sv = serving_of(ctx, &rc);
+  if (!sv) return rc;
+  PinnedPool& pool = sv->pinned;
   {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     tacaw_probe pr = req->probe;
@@ -351,8 +423,8 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
       pr = tacaw_probe{};
       pr.n_probes = 1;
     }
-    int rc = check_run(ctx, &req->params, pr, req->pos, req->Z, req->n_atoms, req->n_frames, req->precision,
-                       req->reduce, req->S_out, true);
+    rc = check_run(ctx, &req->params, pr, req->pos, req->Z, req->n_atoms, req->n_frames, req->precision,
+                   req->reduce, req->S_out, true);
     if (rc != TACAW_OK) return rc;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
@@ -379,7 +451,7 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
       if (on_device(req->pos)) {
         j->pos_dev = req->pos;
       } else {
-        e = cudaMallocHost((void**)&j->pos_pinned, sizeof(float) * j->F * j->A * 3);
+        e = pool.get(sizeof(float) * j->F * j->A * 3, (void**)&j->pos_pinned);
         if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMallocHost");
         std::memcpy(j->pos_pinned, req->pos, sizeof(float) * j->F * j->A * 3);
       }
@@ -387,14 +459,14 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
       if (on_device(req->Z)) e = cudaMemcpy(j->Z.data(), req->Z, sizeof(int32_t) * j->A, cudaMemcpyDeviceToHost);
       else std::memcpy(j->Z.data(), req->Z, sizeof(int32_t) * j->A);
       if (e != cudaSuccess) {
-        if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+        pool.put(j->pos_pinned);
         return cuda_err(ctx, e, "request species");
       }
       for (int64_t i = 0; i < j->A; ++i) {
         bool known = false;
         for (int32_t z : ctx->ffZ) known |= (z == j->Z[i]);
         if (!known) {
-          if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+          pool.put(j->pos_pinned);
           return set_err(ctx, TACAW_EINVAL, "atom %lld has Z=%d, not in the form-factor table", (long long)i,
                          j->Z[i]);
         }
@@ -403,12 +475,14 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
     j->S_user = req->S_out;
     j->S_host = !on_device(req->S_out);
     if (j->S_host) {
-      e = cudaMallocHost((void**)&j->S_pinned, sizeof(float) * j->out_elems);
+      e = pool.get(sizeof(float) * j->out_elems, (void**)&j->S_pinned);
       if (e != cudaSuccess) {
-        if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
+        pool.put(j->pos_pinned);
         return cuda_err(ctx, e, "cudaMallocHost");
       }
     }
+    const double work = (double)pr.n_probes * j->F * j->params.n_slices * j->params.nx * j->params.ny;
+    j->cls = work <= (double)ctx->serving_small_work ? 1 : 0;
     GeoCache* g;
     rc = get_geo(ctx, j->params, &g);
     if (rc == TACAW_OK) {
@@ -418,14 +492,11 @@ int tacaw_submit(tacaw_ctx* ctx, const tacaw_request* req, uint64_t* ticket) {
                      (unsigned long long)j->footprint, (unsigned long long)ctx->budget);
     }
     if (rc != TACAW_OK) {
-      if (j->pos_pinned) cudaFreeHost(j->pos_pinned);
-      if (j->S_pinned) cudaFreeHost(j->S_pinned);
+      pool.put(j->pos_pinned);
+      pool.put(j->S_pinned);
       return rc;
     }
   }
-  int rc = TACAW_OK;
-  Serving* sv = serving_of(ctx, &rc);
-  if (!sv) return rc;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     j->ticket = sv->next_ticket++;
@@ -507,12 +578,26 @@ int tacaw_cancel(tacaw_ctx* ctx, uint64_t ticket) {
       sv->queue.erase(q);
       j.status = TACAW_ECANCELED;
       j.t_done = now_s();
-      if (j.pos_pinned) cudaFreeHost(j.pos_pinned);
-      if (j.S_pinned) cudaFreeHost(j.S_pinned);
+      sv->pinned.put(j.pos_pinned);
+      sv->pinned.put(j.S_pinned);
       j.pos_pinned = j.S_pinned = nullptr;
       sv->cv_done.notify_all();
       break;
     }
+  return TACAW_OK;
+}
+
+int tacaw_serving_hold(tacaw_ctx* ctx, int32_t hold) {
+  if (!ctx) return TACAW_EINVAL;
+  int rc = TACAW_OK;
+  Serving* sv = serving_of(ctx, &rc);
+  if (!sv) return rc;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->hold = hold != 0;
+    sv->kick = true;
+  }
+  sv->cv.notify_all();
   return TACAW_OK;
 }
 

@@ -96,7 +96,8 @@ struct tacaw_ctx {
   int64_t max_run_bytes = 0;     // option: scratch bound of one run (0 = automatic)
   int64_t max_probe_block = 0;   // option: cap on the probes propagated and transformed together
   int64_t max_coalesce = 16;     // option: serving requests of one geometry coalesced into a run
-  int64_t serving_streams = 4;   // option: streams of the serving loop (set before the first submit)
+  int64_t serving_streams = 4;   // option: streams per request class of the serving loop (before the first submit)
+  int64_t serving_small_work = (int64_t)1 << 33;  // option: requests of at most this work are "small"
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };

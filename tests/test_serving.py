@@ -158,8 +158,9 @@ def test_cancel_queued_request(T):
 
 @pytest.mark.parametrize("scan", [False, True])
 def test_same_geometry_requests_share_a_run(T, scan):
-    """Queued requests of one geometry (different trajectories) are coalesced into one run whose
-    launches cover all of them; each result equals the request run alone, bit for bit."""
+    """Requests of one geometry (different trajectories) queued together, here under a hold of
+    admission, are coalesced into runs of at most max_coalesce requests whose launches cover all
+    of them; each result equals the request run alone, bit for bit."""
     import torch
     ws = []
     for k in range(6):
@@ -167,9 +168,7 @@ def test_same_geometry_requests_share_a_run(T, scan):
         if scan:
             w.alpha_mrad, w.probes = 30.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
         ws.append(w)
-    # (of different frame counts: requests of one geometry would be coalesced into one run)
-    blockers = [workloads.config2(n_frames=160 + 16 * k, seed=97 + k) for k in range(4)]
-    fz, fc = table_for(ws + blockers)
+    fz, fc = table_for(ws)
     reduce = T.REDUCE_DETECTOR if scan else T.REDUCE_NONE
     with T.Context(0) as ctx:
         ctx.load_form_factors(fz, fc)
@@ -179,9 +178,12 @@ def test_same_geometry_requests_share_a_run(T, scan):
                         T.probe_of(w), precision=T.DFT_BF16X3, reduce=reduce).cpu().numpy()
             alone.append(S)
         torch.cuda.synchronize()
-        # four longer requests occupy the serving streams, so the six queue up together
-        busy = [submit(T, ctx, w, T.DFT_BF16X3) for w in blockers]
+        T.tacaw_set_option(ctx.h, "max_coalesce", 4)
+        T.tacaw_serving_hold(ctx.h, True)
         subs = [submit(T, ctx, w, T.DFT_BF16X3, host=(i % 3 == 2), reduce=reduce) for i, w in enumerate(ws)]
+        queued, active = T.tacaw_serving_stats(ctx.h)[:2]
+        assert (queued, active) == (6, 0)
+        T.tacaw_serving_hold(ctx.h, False)
         batched = []
         for (t, out, keep), ref in zip(subs, alone):
             rc, r = T.tacaw_wait(ctx.h, t, 300.0)
@@ -189,7 +191,6 @@ def test_same_geometry_requests_share_a_run(T, scan):
             got = out.cpu().numpy() if hasattr(out, "cpu") else out
             assert np.array_equal(got, ref)
             batched.append(r.batched)
-        for t, out, keep in busy:
-            assert T.tacaw_wait(ctx.h, t, 300.0)[0] == T.TACAW_OK
         ctx.check()
-    assert max(batched) > 1, batched
+    # in submission order: the first four share a run, the last two another
+    assert batched == [4, 4, 4, 4, 2, 2], batched
