@@ -331,7 +331,10 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * concurrently (default 4; before the first tacaw_submit only).  "serving_small_work": requests
  * whose work (probes x frames x slices x nx x ny) is at most this (default 2^33) run on
  * high-priority streams of their own, so they wait neither for long requests' streams nor for
- * their pending blocks; the others on normal-priority streams.
+ * their pending blocks; the others on normal-priority streams.  "host_copy": how results reach
+ * page-locked host memory (tacaw_run's S_out, serving requests' host outputs): 1 (default) by
+ * SM stores into the mapped pages, 0 by the copy engine (cudaMemcpyAsync); pageable host
+ * memory always goes through the copy engine.
  * Results do not depend on these options.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 

@@ -152,6 +152,34 @@ ProfScope::~ProfScope() {
   if (cudaEventRecord(rec.b, st) == cudaSuccess) ctx->prof.recs.push_back(rec);
 }
 
+// Results go to page-locked host memory by SM stores by default: right after a run, a copy-engine
+// transfer of c4's 8 GiB S into page-locked memory ran at 16-31 GB/s, the SM copy at 193 GB/s.
+cudaError_t copy_rows_out(tacaw_ctx* ctx, float* dst, size_t dp, const float* src, size_t sp, size_t width,
+                          size_t rows, cudaStream_t st) {
+  if (width == 0 || rows == 0) return cudaSuccess;
+  cudaPointerAttributes a{};
+  const bool known = cudaPointerGetAttributes(&a, dst) == cudaSuccess;
+  if (!known) cudaGetLastError();  // pageable memory: not an error
+  float* target = nullptr;
+  if (known && (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) target = dst;
+  else if (known && a.type == cudaMemoryTypeHost && ctx->host_copy == 1 && a.devicePointer)
+    target = static_cast<float*>(a.devicePointer);
+  if (target) return launch_copy_out(src, (int64_t)sp, target, (int64_t)dp, (int64_t)width, (int64_t)rows, st);
+  return cudaMemcpy2DAsync(dst, sizeof(float) * dp, src, sizeof(float) * sp, sizeof(float) * width, rows,
+                           cudaMemcpyDefault, st);
+}
+
+cudaError_t copy_to_host(tacaw_ctx* ctx, float* dst, const float* src, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  if (ctx->host_copy == 1) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, dst) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
+      return launch_copy_out(src, (int64_t)n, static_cast<float*>(a.devicePointer), (int64_t)n, (int64_t)n, 1, st);
+    cudaGetLastError();  // pageable memory: not an error, the copy engine takes it
+  }
+  return cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+}
+
 constexpr size_t kStagingBytes = (size_t)32 << 20;
 
 cudaError_t staged_copy(tacaw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
@@ -1191,6 +1219,7 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   if (A > 0 && !pos_dev) {
     float* tmp;
     CK(sc.get(&tmp, (size_t)F * A * 3));
+    ProfScope ps(ctx, "h2d_pos", st, (double)sizeof(float) * F * A * 3, 0);
     CK(cudaMemcpyAsync(tmp, pos, sizeof(float) * F * A * 3, cudaMemcpyHostToDevice, st));
     d_pos = tmp;
   }
@@ -1200,7 +1229,10 @@ int tacaw_run(tacaw_ctx* ctx, const tacaw_params* params, const float* pos, cons
   if (!out_dev) CK(sc.get(&d_S, out_elems));
   TRY_RC(run_impl(ctx, p, pr, d_pos, Z, z_dev, A, F, precision, reduce, d_S, st, 1));
   if (!out_dev) {
-    CK(cudaMemcpyAsync(S_out, d_S, sizeof(float) * out_elems, cudaMemcpyDeviceToHost, st));
+    {
+      ProfScope ps(ctx, "d2h_S", st, (double)sizeof(float) * out_elems, 0);
+      CK(copy_to_host(ctx, S_out, d_S, out_elems, st));
+    }
     CK(cudaStreamSynchronize(st));
   } else if (!pos_dev && A > 0) {
     CK(cudaStreamSynchronize(st));  // the caller's host positions were read asynchronously
@@ -1257,6 +1289,11 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (std::strcmp(name, "serving_small_work") == 0) {
     if (value < 0) return set_err(ctx, TACAW_EINVAL, "serving_small_work must be >= 0");
     ctx->serving_small_work = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "host_copy") == 0) {
+    if (value < 0 || value > 1) return set_err(ctx, TACAW_EINVAL, "host_copy must be 0 or 1");
+    ctx->host_copy = value;
     return TACAW_OK;
   }
   if (std::strcmp(name, "max_coalesce") == 0) {

@@ -196,8 +196,7 @@ int launch_batch(Serving& sv, Job& j) {
                     R);
   for (int r = 0; r < R && rc == TACAW_OK; ++r) {
     float* dst = all[r]->S_host ? all[r]->S_pinned : all[r]->S_user;
-    e = cudaMemcpy2DAsync(dst, sizeof(float) * per_out, d_S + per_out * r, sizeof(float) * per_out * R,
-                          sizeof(float) * per_out, (size_t)P, cudaMemcpyDefault, j.stream);
+    e = copy_rows_out(ctx, dst, per_out, d_S + per_out * r, per_out * R, per_out, (size_t)P, j.stream);
     if (e != cudaSuccess) rc = cuda_err(ctx, e, "coalesced output copy");
   }
   if (d_pos) cudaFreeAsync(d_pos, j.stream);
@@ -233,7 +232,7 @@ int launch(Serving& sv, Job& j) {
   }
   int rc = run_impl(ctx, j.params, j.probe, d_pos, j.Z.data(), false, j.A, j.F, j.precision, j.reduce, d_S, j.stream);
   if (rc == TACAW_OK && j.S_host) {
-    e = cudaMemcpyAsync(j.S_pinned, d_S, sizeof(float) * j.out_elems, cudaMemcpyDeviceToHost, j.stream);
+    e = copy_to_host(ctx, j.S_pinned, d_S, j.out_elems, j.stream);
     if (e != cudaSuccess) rc = cuda_err(ctx, e, "request output copy");
   }
   if (j.d_pos_tmp) cudaFreeAsync(j.d_pos_tmp, j.stream);

@@ -98,6 +98,7 @@ struct tacaw_ctx {
   int64_t max_coalesce = 16;     // option: serving requests of one geometry coalesced into a run
   int64_t serving_streams = 4;   // option: streams per request class of the serving loop (before the first submit)
   int64_t serving_small_work = (int64_t)1 << 33;  // option: requests of at most this work are "small"
+  int64_t host_copy = 1;  // option: results into page-locked host memory by 1 SM stores, 0 the copy engine
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;
 };
@@ -150,6 +151,14 @@ struct SpecIO {
 // Host -> device copy of `bytes` from pageable src through the context's pinned ring
 // (asynchronous on st: src may be reused as soon as this returns).  Larger than the ring:
 // a plain copy from pageable memory.
+// n floats from device memory to host memory, stream-ordered: by SM stores when the option
+// "host_copy" is 1 and dst is page-locked and mapped, else by cudaMemcpyAsync.
+cudaError_t copy_to_host(tacaw_ctx* ctx, float* dst, const float* src, size_t n, cudaStream_t st);
+// rows x width floats (pitches in floats) to dst, which may be host or device memory: SM stores
+// for device memory and for mapped page-locked memory under "host_copy" 1, else
+// cudaMemcpy2DAsync.
+cudaError_t copy_rows_out(tacaw_ctx* ctx, float* dst, size_t dp, const float* src, size_t sp, size_t width,
+                          size_t rows, cudaStream_t st);
 cudaError_t staged_copy(tacaw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 int set_err(tacaw_ctx* c, int code, const char* fmt, ...);

@@ -129,6 +129,12 @@ struct SpreadKernel {
 constexpr int TACAW_STATUS_TIMEOUT = 1;  // a kernel's bounded wait ran out
 constexpr int TACAW_STATUS_SPECIES = 2;  // an atom's Z was not in the form-factor table
 
+// rows x width floats, row r of dst_mapped (pitch dp) = row r of src (pitch sp), pitches in
+// floats, by SM stores (dst_mapped: the device address of mapped page-locked host memory, or
+// any device memory).
+cudaError_t launch_copy_out(const float* src, int64_t sp, float* dst_mapped, int64_t dp, int64_t width, int64_t rows,
+                            cudaStream_t st);
+
 // slot[j] = lut[Z[j]] (lut: 256 entries, -1 = not loaded); an unknown Z sets
 // TACAW_STATUS_SPECIES in *status and gets slot 0.
 cudaError_t launch_map_slots(const int32_t* Z, int64_t A, const int8_t* lut, int8_t* slot, int* status,

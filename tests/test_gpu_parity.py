@@ -495,7 +495,10 @@ def test_run_rejects_too_many_frames_or_probes(ctx, T):
     assert ei.value.code == T.TACAW_EINVAL
 
 
-def test_run_host_buffers_match_device(ctx, T):
+@pytest.mark.parametrize("host_copy", [1, 0])
+def test_run_host_buffers_match_device(ctx, T, host_copy):
+    """Host outputs equal the device result bit for bit, by SM stores into page-locked memory
+    (host_copy 1) or by the copy engine (0); pageable outputs take the copy engine either way."""
     import torch
     w = workloads.diamond_si(n_frames=8, grid=32, n_slices=4, seed=43)
     ctx.load_form_factors(w.form_Z, w.form_coef)
@@ -503,9 +506,24 @@ def test_run_host_buffers_match_device(ctx, T):
     S_dev = ctx.run(p, dev(w.pos), dev(w.Z), pr).cpu().numpy()
     pos_h = torch.from_numpy(w.pos).pin_memory()
     Z_h = torch.from_numpy(w.Z)
-    out_h = torch.empty((1, w.n_frames, w.ny, w.nx), dtype=torch.float32).pin_memory()
-    T.tacaw_run(ctx.h, p, pos_h, Z_h, w.n_atoms, w.n_frames, pr, T.DFT_FP32, T.REDUCE_NONE, out_h)
-    assert np.array_equal(out_h.numpy(), S_dev)
+    try:
+        ctx.set_option("host_copy", host_copy)
+        out_h = torch.empty((1, w.n_frames, w.ny, w.nx), dtype=torch.float32).pin_memory()
+        T.tacaw_run(ctx.h, p, pos_h, Z_h, w.n_atoms, w.n_frames, pr, T.DFT_FP32, T.REDUCE_NONE, out_h)
+        assert np.array_equal(out_h.numpy(), S_dev)
+        out_pg = np.full((1, w.n_frames, w.ny, w.nx), -1.0, np.float32)  # pageable
+        T.tacaw_run(ctx.h, p, pos_h, Z_h, w.n_atoms, w.n_frames, pr, T.DFT_FP32, T.REDUCE_NONE, out_pg)
+        assert np.array_equal(out_pg, S_dev)
+        # 7 detector sums into page-locked memory 4 bytes past a 16-byte boundary (scalar stores)
+        w7 = workloads.diamond_si(n_frames=7, grid=32, n_slices=4, seed=44)
+        D_dev = ctx.run(p, dev(w7.pos), dev(w7.Z), pr, reduce=T.REDUCE_DETECTOR).cpu().numpy()
+        buf = torch.full((9,), -1.0, dtype=torch.float32).pin_memory()
+        T.tacaw_run(ctx.h, p, torch.from_numpy(w7.pos).pin_memory(), torch.from_numpy(w7.Z), w7.n_atoms, 7, pr,
+                    T.DFT_FP32, T.REDUCE_DETECTOR, buf[1:8])
+        got = buf.numpy()
+        assert np.array_equal(got[1:8], D_dev.reshape(-1)) and got[0] == -1.0 and got[8] == -1.0
+    finally:
+        ctx.set_option("host_copy", 1)
 
 
 def test_run_is_deterministic(ctx, T):
