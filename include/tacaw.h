@@ -72,10 +72,13 @@ typedef struct tacaw_params {
 } tacaw_params;
 
 /* Illumination (Discussion, "Beyond Vibrational Spectroscopy": aberration function applied
- * at probe formation; arbitrary complex wavefronts).  A convergent probe is
+ * at probe formation, with defocus, astigmatism, coma and spherical aberration; arbitrary
+ * complex wavefronts).  A convergent probe is
  * psi0(k) = A(k) exp(-i chi(k)) exp(-2 pi i k.r_p) / norm with A = 1 for |k| <= alpha/lambda and
- * chi(k) = pi lambda k^2 (defocus + astig cos 2(phi_k - astig_angle)) + (pi/2) Cs lambda^3 k^4,
- * so a positive defocus equals free propagation over that distance. */
+ * chi(k) = pi lambda k^2 (defocus + astig cos 2(phi_k - astig_angle))
+ *        + (2 pi / 3) coma lambda^2 k^3 cos(phi_k - coma_angle) + (pi/2) Cs lambda^3 k^4,
+ * i.e. (2 pi / lambda) (C1 theta^2 / 2 + C21 theta^3 / 3 + C3 theta^4 / 4) at theta = lambda k, so
+ * a positive defocus equals free propagation over that distance. */
 typedef struct tacaw_probe {
   double alpha_mrad;   /* convergence semi-angle; <= 0: plane wave (n_probes must be 1) */
   int32_t n_probes;    /* P >= 1 */
@@ -87,6 +90,8 @@ typedef struct tacaw_probe {
   double astig_angle;  /* rad */
   const float* psi0;   /* DEVICE c64 [P][ny][nx]: real-space initial waves to use instead of the
                           aperture probe (e.g. vortex beams), normalised by the caller; NULL: none */
+  double coma;         /* axial coma C21, A */
+  double coma_angle;   /* rad */
 } tacaw_probe;
 
 /* Library version string (static storage). */

@@ -95,7 +95,7 @@ def lib():
                 "oracle_dispersion": (None, [dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp,
                                              dp, C.c_int, dp]),
                 "oracle_probe_aberrated": (None, [pp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                                  C.c_double, C.c_double, vp]),
+                                                  C.c_double, C.c_double, C.c_double, C.c_double, vp]),
                 "oracle_multislice_frame_init": (C.c_int, [pp, fp, ip, C.c_int, ip, dp, C.c_int, vp, C.c_int, vp]),
             }
             for name, (res, args) in sig.items():
@@ -288,10 +288,10 @@ def dispersion(S, cell, kx, ky):
     return out
 
 
-def probe_aberrated(p: Params, alpha_mrad, xp=0.0, yp=0.0, df=0.0, cs_mm=0.0, a1=0.0, phi_a=0.0):
+def probe_aberrated(p: Params, alpha_mrad, xp=0.0, yp=0.0, df=0.0, cs_mm=0.0, a1=0.0, phi_a=0.0, b2=0.0, phi_b=0.0):
     psi = np.zeros((p.ny, p.nx), dtype=np.complex128)
     lib().oracle_probe_aberrated(C.byref(p), float(alpha_mrad), float(xp), float(yp), float(df), float(cs_mm),
-                                 float(a1), float(phi_a), psi.ctypes.data)
+                                 float(a1), float(phi_a), float(b2), float(phi_b), psi.ctypes.data)
     return psi
 
 

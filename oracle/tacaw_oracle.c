@@ -487,11 +487,15 @@ void oracle_dispersion(const double *S, int P, int F, int ny, int nx, double Lx,
         }
 }
 
-/* Convergent probe with aberrations: psi0(k) = A(k) exp(-i chi(k)) exp(-2 pi i k.r_p) / norm,
- * chi = pi lambda k^2 (df + a1 cos 2(phi - phi_a)) + (pi/2) Cs lambda^3 k^4 (df, a1 in A,
- * Cs in mm), then a unitary inverse transform.  With chi = 0 this is oracle_probe. */
+/* Convergent probe with aberrations (Discussion, "Beyond Vibrational Spectroscopy": the
+ * standard aberration function with defocus, astigmatism, coma and spherical aberration):
+ * psi0(k) = A(k) exp(-i chi(k)) exp(-2 pi i k.r_p) / norm, with, at theta = lambda k,
+ * chi = (2 pi / lambda) (df theta^2 / 2 + a1 theta^2 cos 2(phi - phi_a) / 2
+ *                        + b2 theta^3 cos(phi - phi_b) / 3 + Cs theta^4 / 4)
+ * (df, a1, b2 in A, Cs in mm), then a unitary inverse transform.  With chi = 0 this is
+ * oracle_probe. */
 void oracle_probe_aberrated(const oracle_params *p, double alpha_mrad, double xp, double yp, double df_A,
-                            double cs_mm, double a1_A, double phi_a, cplx *psi) {
+                            double cs_mm, double a1_A, double phi_a, double b2_A, double phi_b, cplx *psi) {
     const int nx = p->nx, ny = p->ny;
     const size_t nq = (size_t)nx * ny;
     const double lam = oracle_wavelength(p->voltage_ev);
@@ -502,8 +506,11 @@ void oracle_probe_aberrated(const oracle_params *p, double alpha_mrad, double xp
             double kx = oracle_kfreq(ix, nx, p->Lx), ky = oracle_kfreq(iy, ny, p->Ly);
             double k2 = kx * kx + ky * ky;
             int in = k2 <= kmax * kmax;
-            double chi = M_PI * lam * k2 * (df_A + a1_A * cos(2.0 * (atan2(ky, kx) - phi_a))) +
-                         0.5 * M_PI * cs * lam * lam * lam * k2 * k2;
+            double theta = lam * sqrt(k2), phi = atan2(ky, kx);
+            double chi = (2.0 * M_PI / lam) * (0.5 * df_A * theta * theta +
+                                               0.5 * a1_A * theta * theta * cos(2.0 * (phi - phi_a)) +
+                                               b2_A * theta * theta * theta * cos(phi - phi_b) / 3.0 +
+                                               0.25 * cs * theta * theta * theta * theta);
             psi[(size_t)iy * nx + ix] = in ? cexp(-I * chi) * cexp(-2.0 * M_PI * I * kx * xp) *
                                                  cexp(-2.0 * M_PI * I * ky * yp)
                                            : 0.0;

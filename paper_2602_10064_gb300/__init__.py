@@ -46,7 +46,7 @@ class Params(C.Structure):
 class Probe(C.Structure):
     _fields_ = [("alpha_mrad", C.c_double), ("n_probes", C.c_int32), ("pad_", C.c_int32), ("xy", C.c_void_p),
                 ("defocus", C.c_double), ("cs_mm", C.c_double), ("astig", C.c_double), ("astig_angle", C.c_double),
-                ("psi0", C.c_void_p)]
+                ("psi0", C.c_void_p), ("coma", C.c_double), ("coma_angle", C.c_double)]
 
 
 def make_params(nx, ny, n_slices, cell, voltage_ev=100e3, bandlimit=2.0 / 3.0, bandlimit_transmission=1,
@@ -81,7 +81,8 @@ class ProbeSpec:
     """A tacaw_probe plus the buffers its pointers refer to.  psi0: optional device complex64
     tensor [P][ny][nx] of real-space initial waves used instead of the aperture probe."""
 
-    def __init__(self, alpha_mrad=0.0, xy=None, defocus=0.0, cs_mm=0.0, astig=0.0, astig_angle=0.0, psi0=None):
+    def __init__(self, alpha_mrad=0.0, xy=None, defocus=0.0, cs_mm=0.0, astig=0.0, astig_angle=0.0, psi0=None,
+                 coma=0.0, coma_angle=0.0):
         self.xy = None if xy is None else np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
         self.psi0 = psi0
         n = 1 if self.xy is None else self.xy.shape[0]
@@ -89,7 +90,7 @@ class ProbeSpec:
             n = psi0.shape[0]
         self.c = Probe(float(alpha_mrad), n, 0, None if self.xy is None else self.xy.ctypes.data, float(defocus),
                        float(cs_mm), float(astig), float(astig_angle),
-                       None if psi0 is None else _ptr(psi0))
+                       None if psi0 is None else _ptr(psi0), float(coma), float(coma_angle))
 
     @property
     def n_probes(self):

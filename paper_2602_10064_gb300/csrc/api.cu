@@ -292,7 +292,7 @@ tacaw_probe default_probe() {
 }
 
 bool has_aberrations(const tacaw_probe& pr) {
-  return pr.defocus != 0.0 || pr.cs_mm != 0.0 || pr.astig != 0.0;
+  return pr.defocus != 0.0 || pr.cs_mm != 0.0 || pr.astig != 0.0 || pr.coma != 0.0;
 }
 
 int check_params(tacaw_ctx* ctx, const tacaw_params* p) {
@@ -792,8 +792,9 @@ int build_probes(tacaw_ctx* ctx, const tacaw_params& p, const tacaw_probe& pr, S
       const int x = c <= mb ? c : nx - (W - c);
       const double kx = kfreq(x, nx, Lx);
       for (int y = 0; y < ny; ++y) {
-        const double ky = kfreq(y, ny, Ly), k2 = kx * kx + ky * ky;
-        const double ph = M_PI * lam * k2 * (pr.defocus + pr.astig * std::cos(2.0 * (std::atan2(ky, kx) - pr.astig_angle))) +
+        const double ky = kfreq(y, ny, Ly), k2 = kx * kx + ky * ky, phk = std::atan2(ky, kx);
+        const double ph = M_PI * lam * k2 * (pr.defocus + pr.astig * std::cos(2.0 * (phk - pr.astig_angle))) +
+                          (2.0 * M_PI / 3.0) * pr.coma * lam * lam * k2 * std::sqrt(k2) * std::cos(phk - pr.coma_angle) +
                           0.5 * M_PI * cs * lam * lam * lam * k2 * k2;
         chi[(size_t)y * Wp + c] = make_float2((float)std::cos(ph), (float)-std::sin(ph));
       }

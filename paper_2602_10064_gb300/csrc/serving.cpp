@@ -164,7 +164,8 @@ bool same_geometry(const Job& a, const Job& b) {
          a.precision == b.precision && a.reduce == b.reduce && a.probe.alpha_mrad == b.probe.alpha_mrad &&
          a.probe.n_probes == b.probe.n_probes && a.probe.defocus == b.probe.defocus &&
          a.probe.cs_mm == b.probe.cs_mm && a.probe.astig == b.probe.astig &&
-         a.probe.astig_angle == b.probe.astig_angle && a.probe.psi0 == b.probe.psi0 && a.probe_xy == b.probe_xy &&
+         a.probe.astig_angle == b.probe.astig_angle && a.probe.coma == b.probe.coma &&
+         a.probe.coma_angle == b.probe.coma_angle && a.probe.psi0 == b.probe.psi0 && a.probe_xy == b.probe_xy &&
          a.Z == b.Z;
 }
 

@@ -78,14 +78,15 @@ def test_trajectory_averaging(ctx, T):
 def test_aberrated_probe_scan(ctx, T):
     w = workloads.diamond_si(n_frames=2, grid=64, n_slices=4, seed=64)
     xy = np.array([[0.5, 1.0], [3.0, 6.5]])
-    ab = dict(defocus=25.0, cs_mm=1.2, astig=15.0, astig_angle=0.4)
+    ab = dict(defocus=25.0, cs_mm=1.2, astig=15.0, astig_angle=0.4, coma=900.0, coma_angle=1.1)
     ctx.load_form_factors(w.form_Z, w.form_coef)
     p = T.params_of(w)
     V = ctx.build_potential(p, dev(w.pos), dev(w.Z))
     psi = ctx.propagate(p, V, T.ProbeSpec(30.0, xy, **ab)).cpu().numpy()
     op = oracle.params_of(w)
     psi0 = np.stack([oracle.probe_aberrated(op, 30.0, x, y, df=ab["defocus"], cs_mm=ab["cs_mm"], a1=ab["astig"],
-                                            phi_a=ab["astig_angle"]) for x, y in xy])
+                                            phi_a=ab["astig_angle"], b2=ab["coma"], phi_b=ab["coma_angle"])
+                     for x, y in xy])
     for f in range(2):
         ref = oracle.multislice_frame_init(op, w.pos[f], w.Z, w.form_Z, w.form_coef, psi0)
         assert rel(psi[:, f], ref) < 2e-5

@@ -540,6 +540,43 @@ def test_spherical_aberration_textbook_angular_form(cs_mm):
     assert np.abs(chi[inside]).max() / abs(cs_mm) > 50.0
 
 
+@pytest.mark.parametrize("b2,phi_b", [(2000.0, 0.0), (-3000.0, 0.7), (5000.0, 2.5)])
+def test_coma_cartesian_form(b2, phi_b):
+    # Axial coma, (2 pi / lambda) C21 theta^3 cos(phi - phi_b) / 3 at theta = lambda |k|, written
+    # without angles: (2 pi / 3) C21 lambda^2 |k|^2 (kx cos phi_b + ky sin phi_b).  A 1/2 in place
+    # of 1/3, a power of |k| off by one, cos(2 phi) in place of cos(phi), or a flipped sign fails.
+    N, L, alpha = 96, 24.0, 30.0
+    p = oracle.params(N, N, 1, (L, L, 2.0), bandlimit=0.0)
+    lam = oracle.wavelength(100e3)
+    KX, KY, inside = _aperture_coefficients(N, L, alpha, lam)
+    chi = (2 * np.pi / 3) * b2 * lam ** 2 * (KX ** 2 + KY ** 2) * (KX * np.cos(phi_b) + KY * np.sin(phi_b))
+    got = _unitary_k(oracle.probe_aberrated(p, alpha, b2=b2, phi_b=phi_b))
+    amp = 1.0 / math.sqrt(inside.sum())
+    assert np.abs(got[inside] - amp * np.exp(-1j * chi[inside])).max() < 1e-11
+    assert np.abs(got[~inside]).max() < 1e-12
+    # the coma phase spans radians across the aperture
+    assert np.abs(chi[inside]).max() > 1.0
+
+
+def test_coma_is_odd_and_the_other_terms_even():
+    # chi(-k) = -chi(k) for coma and +chi(k) for defocus, astigmatism and Cs, so for a centred
+    # probe c(k) c(-k) = amp^2 exp(-2 i chi_even(k)): the coma term cancels from the product and
+    # the even terms remain.
+    N, L, alpha = 64, 16.0, 28.0
+    p = oracle.params(N, N, 1, (L, L, 2.0), bandlimit=0.0)
+    lam = oracle.wavelength(100e3)
+    ab = dict(df=20.0, cs_mm=0.9, a1=12.0, phi_a=0.4)
+    even = _unitary_k(oracle.probe_aberrated(p, alpha, **ab))
+    both = _unitary_k(oracle.probe_aberrated(p, alpha, b2=1200.0, phi_b=1.1, **ab))
+    flip = lambda c: np.roll(c[::-1, ::-1], 1, axis=(0, 1))  # c(-k) on the fftfreq grid
+    assert np.abs(both * flip(both) - even * flip(even)).max() < 1e-14
+    # and the coma does change the probe
+    assert np.abs(both - even).max() > 1e-3
+    # coma alone: c(-k) = conj(c(k))
+    coma = _unitary_k(oracle.probe_aberrated(p, alpha, b2=1200.0, phi_b=1.1))
+    assert np.abs(flip(coma) - np.conj(coma)).max() < 1e-14
+
+
 def test_multislice_from_initial_waves_matches_probe_path():
     w = workloads.diamond_si(n_frames=1, grid=32, n_slices=3)
     p = oracle.params_of(w)
