@@ -54,6 +54,8 @@ def make_workload(name, seed_offset=0, frames=None, probes=None):
         w = workloads.config4(n_frames=frames or 2048, seed=4 + seed_offset)
     elif name == "m1":
         w = workloads.minimal_example_si(n_frames=frames or 200, seed=6 + seed_offset)
+    elif name == "m1s":  # the minimal example's 32 x 32 scan at 30 mrad
+        w = workloads.minimal_example_si(n_frames=frames or 200, seed=6 + seed_offset, n_scan=32)
     else:
         raise SystemExit(f"unknown workload {name}")
     if probes and w.alpha_mrad > 0 and probes < w.n_probes:
@@ -453,7 +455,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "m1"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "m1", "m1s"])
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

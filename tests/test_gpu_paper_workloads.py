@@ -95,3 +95,22 @@ def test_minimal_example_geometry_sampled_frames(ctx, T):
         err = rel(psi[i], refs[i])
         print(f"minimal example, frame {frames[i]}: exit wave rel L2 = {err:.2e}")
         assert err < TOL_FIELD, err
+
+
+def test_minimal_example_scan_sampled_probes(ctx, T):
+    # the minimal example's 32 x 32 scan at 30 mrad: two of its probes, two frames
+    w = workloads.minimal_example_si(n_frames=8, n_scan=32)
+    assert w.n_probes == 1024 and w.alpha_mrad == 30.0
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p = T.params_of(w)
+    frames, sel = [1, 6], [0, 529]
+    xy = w.probes[sel]
+    V = ctx.build_potential(p, dev(w.pos[frames]), dev(w.Z))
+    psi = ctx.propagate(p, V, T.ProbeSpec(w.alpha_mrad, xy)).cpu().numpy()
+    refs = oracle.multislice(oracle.params_of(w), w.pos[frames], w.Z, w.form_Z, w.form_coef,
+                             alpha_mrad=w.alpha_mrad, probes=xy)
+    for j in range(len(sel)):
+        for i in range(len(frames)):
+            err = rel(psi[j, i], refs[j, i])
+            print(f"minimal example scan, probe {sel[j]}, frame {frames[i]}: exit wave rel L2 = {err:.2e}")
+            assert err < TOL_FIELD, err
