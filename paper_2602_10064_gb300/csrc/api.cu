@@ -848,7 +848,7 @@ int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, 
       const double in = s > 0 ? W8 : (psi0 ? 8.0 * p.nx : 0.0), tin = tfused ? W8 : 8.0 * p.nx;
       ProfScope ps(ctx, "slice_row", sc.st, rows * (in + tin + W8), rows * ((s > 0 ? 2 : 1) + (tfused ? 1 : 0)) * fx);
       CK(launch_slice_row(geo, g->band, s == 0, psi0 == nullptr, tfused, Apsi, psi0, t, t_slices, s - t_first, P,
-                          nfc, plane_amp, Bpsi, sc.st));
+                          nfc, plane_amp, Bpsi, (int)ctx->static_band, sc.st));
     }
     {
       const double out = last && compact ? (double)g->nsel * 8.0 * P * nfc : rows * W8;
@@ -1290,6 +1290,11 @@ int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value) {
   if (std::strcmp(name, "serving_small_work") == 0) {
     if (value < 0) return set_err(ctx, TACAW_EINVAL, "serving_small_work must be >= 0");
     ctx->serving_small_work = value;
+    return TACAW_OK;
+  }
+  if (std::strcmp(name, "static_band") == 0) {
+    if (value < 0 || value > 1) return set_err(ctx, TACAW_EINVAL, "static_band must be 0 or 1");
+    ctx->static_band = value;
     return TACAW_OK;
   }
   if (std::strcmp(name, "host_copy") == 0) {

@@ -153,6 +153,58 @@ __device__ __forceinline__ void store_row_compact(const float2 (&v)[E], float2* 
   }
 }
 
+// The same with the band's half-width MB known at compile time (W = 2 MB + 1): the element e of
+// every thread covers positions [T e, T e + T), so whether it is in band, out of band or split
+// is decided per e at compile time, and only the split elements keep a per-thread test.
+template <int N, int E, int MB>
+__device__ __forceinline__ void load_row_band(float2 (&v)[E], const float2* __restrict__ src, int t) {
+  constexpr int T = N / E, W = 2 * MB + 1;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int x = t + T * e;
+    if (T * e + T - 1 <= MB) {
+      v[e] = src[x];
+    } else if (T * e >= N - MB) {
+      v[e] = src[x - N + W];
+    } else if (T * e > MB && T * e + T - 1 < N - MB) {
+      v[e] = make_float2(0.f, 0.f);
+    } else {
+      const int c = x <= MB ? x : (x >= N - MB ? x - N + W : -1);
+      v[e] = c >= 0 ? src[c] : make_float2(0.f, 0.f);
+    }
+  }
+}
+
+template <int N, int E, int MB>
+__device__ __forceinline__ void store_row_band(const float2 (&v)[E], float2* __restrict__ dst, int t) {
+  constexpr int T = N / E, W = 2 * MB + 1;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int x = t + T * e;
+    if (T * e + T - 1 <= MB) {
+      dst[x] = v[e];
+    } else if (T * e >= N - MB) {
+      dst[x - N + W] = v[e];
+    } else if (!(T * e > MB && T * e + T - 1 < N - MB)) {
+      const int c = x <= MB ? x : (x >= N - MB ? x - N + W : -1);
+      if (c >= 0) dst[c] = v[e];
+    }
+  }
+}
+
+// The compact row accessors with the band's half-width fixed at compile time (MB >= 0) or
+// read from b (MB < 0).
+template <int N, int MB, int E>
+__device__ __forceinline__ void load_row(float2 (&v)[E], const float2* __restrict__ src, const Band& b, int t) {
+  if constexpr (MB >= 0) load_row_band<N, E, MB>(v, src, t);
+  else load_row_compact<N>(v, src, b, t);
+}
+template <int N, int MB, int E>
+__device__ __forceinline__ void store_row(const float2 (&v)[E], float2* __restrict__ dst, const Band& b, int t) {
+  if constexpr (MB >= 0) store_row_band<N, E, MB>(v, dst, t);
+  else store_row_compact<N>(v, dst, b, t);
+}
+
 // ============================================================================================
 // a1: slice binning.  One CTA per frame; stable scatter, so every slice list keeps atom order.
 // ============================================================================================
@@ -733,7 +785,9 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <int NX, bool FIRST, bool PLANE, bool TF>
+// MB >= 0: the band's half-width, fixed at compile time (the standard 2/3 band of a square
+// cell, MB = NX / 3); MB < 0: read from b.
+template <int NX, bool FIRST, bool PLANE, bool TF, int MB = -1>
 __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW, NX, SliceRowCfg<NX>>())
     k_slice_row(Geo geo, Band b, const float2* __restrict__ Apsi, const float2* __restrict__ psi0,
                 const float2* __restrict__ ttab, int S, int s, int nfc, int nwaves, float plane_amp,
@@ -763,7 +817,7 @@ __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW,
   // copied asynchronously at once, so its load overlaps the wave's load and inverse transform.
   float2* tst = reinterpret_cast<float2*>(smraw + SliceRowCfg<NX>::SMEM) + g * NX;
   if (TF) {
-    load_row_compact<NX>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
+    load_row<NX, MB>(v, ttab + ((size_t)(fl * S + s) * ny + y) * b.Wp, b, t);
     fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
 #pragma unroll
     for (int e = 0; e < E; ++e) tst[t + T * e] = v[e];
@@ -784,14 +838,14 @@ __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW,
       for (int e = 0; e < E; ++e) v[e] = cmul(src[t + T * e], tst[t + T * e]);
     }
   } else {
-    load_row_compact<NX>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
+    load_row<NX, MB>(v, Apsi + ((size_t)w * ny + y) * b.Wp, b, t);
     fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
     if (!TF) cp_async_wait_all();
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = cmul(v[e], tst[t + T * e]);
   }
   fft<NX, -1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
-  store_row_compact<NX>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
+  store_row<NX, MB>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
 }
 
 template <int NY, bool LAST>
@@ -1033,7 +1087,7 @@ cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, in
 template <int NX>
 static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                                const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
-                               float2* Bpsi, cudaStream_t st) {
+                               float2* Bpsi, int static_band, cudaStream_t st) {
   const int nw = P * nfc;
   const dim3 grid = batch_grid(g.ny / SliceRowCfg<NX>::G, nw);
   constexpr int TH = SliceRowCfg<NX>::THREADS;
@@ -1044,22 +1098,42 @@ static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane
     if (e_ != cudaSuccess) return e_;                                                                             \
     k_slice_row<NX, F, PL, TFU><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp, Bpsi);        \
   } while (0)
+  // the later slices (all but one of S) with the standard band fixed at compile time
+  constexpr int MB3 = NX / 3;
+  constexpr bool SPEC = fft_pow2(NX) && NX >= 128 && NX <= 1024;
+  const bool std_band = static_band && SPEC && b.mb == MB3 && b.W == 2 * MB3 + 1;
+#define TACAW_SLICE_ROW_STD(TFU)                                                                                   \
+  do {                                                                                                            \
+    constexpr int SM = SliceRowSmem<NX, TFU>::BYTES;                                                              \
+    cudaError_t e_ = prep(k_slice_row<NX, false, false, TFU, MB3>, SM);                                           \
+    if (e_ != cudaSuccess) return e_;                                                                             \
+    k_slice_row<NX, false, false, TFU, MB3><<<grid, TH, SM, st>>>(g, b, Apsi, psi0, t, S, s, nfc, nw, plane_amp,  \
+                                                                  Bpsi);                                          \
+  } while (0)
   if (tfused) {
     if (first && plane) TACAW_SLICE_ROW(true, true, true);
     else if (first) TACAW_SLICE_ROW(true, false, true);
-    else TACAW_SLICE_ROW(false, false, true);
+    else if constexpr (SPEC) {
+      if (std_band) TACAW_SLICE_ROW_STD(true);
+      else TACAW_SLICE_ROW(false, false, true);
+    } else TACAW_SLICE_ROW(false, false, true);
   } else {
     if (first && plane) TACAW_SLICE_ROW(true, true, false);
     else if (first) TACAW_SLICE_ROW(true, false, false);
-    else TACAW_SLICE_ROW(false, false, false);
+    else if constexpr (SPEC) {
+      if (std_band) TACAW_SLICE_ROW_STD(false);
+      else TACAW_SLICE_ROW(false, false, false);
+    } else TACAW_SLICE_ROW(false, false, false);
   }
+#undef TACAW_SLICE_ROW_STD
 #undef TACAW_SLICE_ROW
   return cudaGetLastError();
 }
 cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                              const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
-                             float2* Bpsi, cudaStream_t st) {
-  TACAW_DISPATCH(g.nx, slice_row_n, g, b, first, plane, tfused, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi, st);
+                             float2* Bpsi, int static_band, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, slice_row_n, g, b, first, plane, tfused, Apsi, psi0, t, S, s, P, nfc, plane_amp, Bpsi,
+                 static_band, st);
 }
 
 template <int NY>

@@ -98,6 +98,7 @@ struct tacaw_ctx {
   int64_t max_coalesce = 16;     // option: serving requests of one geometry coalesced into a run
   int64_t serving_streams = 4;   // option: streams per request class of the serving loop (before the first submit)
   int64_t serving_small_work = (int64_t)1 << 33;  // option: requests of at most this work are "small"
+  int64_t static_band = 1;  // option: later-slice row passes built for the standard band (1) or not (0)
   int64_t host_copy = 1;  // option: results into page-locked host memory by 1 SM stores, 0 the copy engine
   std::vector<void*> owned;
   tacaw::Serving* serving = nullptr;

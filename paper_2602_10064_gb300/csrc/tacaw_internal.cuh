@@ -171,9 +171,11 @@ cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, in
                              cudaStream_t st);
 // One slice s for n_waves = P * nfc waves; wave w = p * nfc + fl uses t[(fl * S + s)], full
 // rows, or with tfused the compact band-limit column-pass output, inverse-transformed in place.
+// static_band: the later slices use the kernel built for the standard 2/3 band of a square cell
+// (half-width NX / 3 fixed at compile time) when b is that band.
 cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                              const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
-                             float2* Bpsi, cudaStream_t st);
+                             float2* Bpsi, int static_band, cudaStream_t st);
 // last = 0: Apsi = IFFT_y(P M scale FFT_y(Bpsi)); last = 1: psi_k[p][f0 + fl] = P M scale FFT_y(Bpsi),
 // as the full [ny][nx] grid (disc = NULL; out-of-band points are not written) or, with disc, as
 // the nsel in-band points of the disc in ascending q: row y's points start at disc[y].x and

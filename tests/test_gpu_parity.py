@@ -534,6 +534,29 @@ def test_run_is_deterministic(ctx, T):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("grid,probe", [(128, False), (256, True), (512, False)])
+def test_fixed_band_row_pass_gives_the_same_bits(ctx, T, grid, probe):
+    """The later slices' row pass built for the standard 2/3 band (option static_band 1, used
+    here: square cells) and the one that reads the band at run time give the same bits; the
+    result is held to the oracle by the other parity tests."""
+    w = workloads.diamond_si(n_frames=3, grid=grid, n_slices=5, seed=47)
+    if probe:
+        w.alpha_mrad, w.probes = 25.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
+    ctx.load_form_factors(w.form_Z, w.form_coef)
+    p, pr = T.params_of(w), T.probe_of(w)
+    x = T.tacaw_band_points(ctx.h, p) % grid
+    assert x[x < grid // 2].max() == grid // 3  # the standard band: the fixed-band kernel runs
+    pos, Z = dev(w.pos), dev(w.Z)
+    try:
+        ctx.set_option("static_band", 1)
+        fixed = ctx.run(p, pos, Z, pr).cpu().numpy()
+        ctx.set_option("static_band", 0)
+        runtime = ctx.run(p, pos, Z, pr).cpu().numpy()
+    finally:
+        ctx.set_option("static_band", 1)
+    assert np.array_equal(fixed, runtime)
+
+
 @pytest.mark.parametrize("probe", [False, True])
 def test_run_tiling_does_not_change_result(ctx, T, probe):
     """Frame chunks and slice blocks only regroup independent (frame, slice) work and carry the
