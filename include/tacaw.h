@@ -339,9 +339,10 @@ int tacaw_spectrum_static(const float* psi_k, int64_t P, int64_t F, int64_t nq, 
  * their pending blocks; the others on normal-priority streams.  "host_copy": how results reach
  * page-locked host memory (tacaw_run's S_out, serving requests' host outputs): 1 (default) by
  * SM stores into the mapped pages, 0 by the copy engine (cudaMemcpyAsync); pageable host
- * memory always goes through the copy engine.  "static_band": 1 (default) runs the later slices'
- * row pass with a kernel built for the standard 2/3 band of a square cell when the run's band is
- * that one, 0 always reads the band at run time.
+ * memory always goes through the copy engine.  "static_band": 1 (default) runs the row passes that
+ * read or write in-band rows (spreading, potential output, the later slices) with kernels built
+ * for the standard 2/3 band of a square cell when the run's band is that one; 0 always reads
+ * the band at run time.
  * Results do not depend on these options.  EINVAL for an unknown name or a bad value. */
 int tacaw_set_option(tacaw_ctx* ctx, const char* name, int64_t value);
 

@@ -660,7 +660,7 @@ int potential_block(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const Bi
     ProfScope ps(ctx, "splat_row", st, (double)nfc * A * 16 * sbc / S + (double)nfs * g->npair * ny * W8,
                  (double)nfs * g->npair * ny * fx);
     CK(launch_splat_row(geo, g->band, bn.rrecs + (size_t)f0 * A, bn.boffs + (size_t)f0 * S * (nyb + 1), A, S, s0,
-                        sbc, nfs, g->npair, sk, Bp, st));
+                        sbc, nfs, g->npair, sk, Bp, (int)ctx->static_band, st));
   }
   {
     ProfScope ps(ctx, "col_pot", st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
@@ -732,7 +732,7 @@ int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const 
   if (!bl) {
     if (Ap) {
       ProfScope ps(ctx, "row_pot_t", sc.st, row * (W8 + 8.0 * p.nx), row * fx);
-      CK(launch_row_pot_out(geo, g->band, Ap, nfs, 2, sig, nullptr, t, sc.st));
+      CK(launch_row_pot_out(geo, g->band, Ap, nfs, 2, sig, nullptr, t, (int)ctx->static_band, sc.st));
     } else {
       ProfScope ps(ctx, "row_vt", sc.st, row * 12.0 * p.nx, 0);
       CK(launch_row_vt(geo, g->band, V, nfs, 0, sig, t, sc.st));
@@ -743,7 +743,7 @@ int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const 
   float2* At = compact ? t : tb.At;
   if (Ap) {
     ProfScope ps(ctx, "row_pot_t", sc.st, row * 2 * W8, row * 2 * fx);
-    CK(launch_row_pot_out(geo, g->band, Ap, nfs, 1, sig, nullptr, Bt, sc.st));
+    CK(launch_row_pot_out(geo, g->band, Ap, nfs, 1, sig, nullptr, Bt, (int)ctx->static_band, sc.st));
   } else {
     ProfScope ps(ctx, "row_vt", sc.st, row * (4.0 * p.nx + W8), row * fx);
     CK(launch_row_vt(geo, g->band, V, nfs, 1, sig, Bt, sc.st));
@@ -1115,7 +1115,7 @@ int tacaw_build_potential(tacaw_ctx* ctx, const tacaw_params* params, const floa
   return potential_chunks(ctx, p, g, pos, slots, n_atoms, nf, chunk, p.n_slices, sc,
                           [&](int64_t f0, int nfc, int, int, float2* Ap) {
     CK(launch_row_pot_out(geo, g->band, Ap, nfc * p.n_slices, 0, 0.f,
-                          V_out + (size_t)f0 * p.n_slices * p.ny * p.nx, nullptr, st));
+                          V_out + (size_t)f0 * p.n_slices * p.ny * p.nx, nullptr, (int)ctx->static_band, st));
     return TACAW_OK;
   });
 }

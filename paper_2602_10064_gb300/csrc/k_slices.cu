@@ -436,7 +436,7 @@ struct SplatSmem {
   static constexpr int BYTES = (ACC + TAB) > SplatCfg<NX>::SMEM ? (ACC + TAB) : SplatCfg<NX>::SMEM;
 };
 
-template <int NX>
+template <int NX, int MB = -1>
 __global__ void __launch_bounds__(SplatCfg<NX>::THREADS, minb_of<K_SPLAT_ROW, NX, SplatCfg<NX>>())
     k_splat_row(Geo geo, Band b, const AtomRec* __restrict__ recs, const int* __restrict__ boffs, int A, int S,
                 int s0, int sb, int npair, int nbatch, SpreadKernel sk, float2* __restrict__ Bp) {
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(SplatCfg<NX>::THREADS, minb_of<K_SPLAT_ROW, NX
   __syncthreads();  // the FFT scratch of one group overlaps the accumulators of the next
   fft<NX, -1, PL>(v, sm, RowIdx<NX, E>{g * row_smem_stride<NX, E>()}, t, geo.tw + tw_offset(NX),
                   group_sync<T>(g));
-  store_row_compact<NX>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
+  store_row<NX, MB>(v, Bp + ((size_t)bidx * ny + y0 + g) * b.Wp, b, t);
 }
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(ColPotCfg<NY>::THREADS, minb_of<K_COL_POT, NY,
 
 // Row pass out of the potential: IFFT_x, real part = V.  mode 0 stores V; mode 1 forms
 // t = exp(i sigma V) and runs FFT_x for the transmission band limit; mode 2 stores t.
-template <int NX>
+template <int NX, int MB = -1>
 __global__ void __launch_bounds__(PotOutCfg<NX>::THREADS, minb_of<K_ROW_POT_OUT, NX, PotOutCfg<NX>>())
     k_row_pot_out(Geo geo, Band b, const float2* __restrict__ Ap, int nbatch, int mode, float sigma,
                   float* __restrict__ V, float2* __restrict__ out) {
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(PotOutCfg<NX>::THREADS, minb_of<K_ROW_POT_OUT,
   const RowIdx<NX, E> idx{g * row_smem_stride<NX, E>()};
   const auto sync = group_sync<T>(g);
   float2 v[E];
-  load_row_compact<NX>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
+  load_row<NX, MB>(v, Ap + ((size_t)fs * ny + y) * b.Wp, b, t);
   fft<NX, +1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
   const size_t row = ((size_t)fs * ny + y) * NX;
   if (mode == 0) {
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(PotOutCfg<NX>::THREADS, minb_of<K_ROW_POT_OUT,
     return;
   }
   fft<NX, -1, PL>(v, sm, idx, t, geo.tw + tw_offset(NX), sync);
-  store_row_compact<NX>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
+  store_row<NX, MB>(v, out + ((size_t)fs * ny + y) * b.Wp, b, t);
 }
 
 // ============================================================================================
@@ -952,6 +952,18 @@ static cudaError_t prep(K kernel, int smem) {
   return cudaSuccess;
 }
 
+// Row-pass kernels are also built for the standard 2/3 band of a square cell (half-width NX / 3
+// fixed at compile time) at these lengths; a launch uses that build when its band is that one
+// and the context option "static_band" is on.
+template <int NX>
+constexpr bool std_band_built() {
+  return fft_pow2(NX) && NX >= 128 && NX <= 1024;
+}
+template <int NX>
+bool std_band(const Band& b, int static_band) {
+  return static_band && std_band_built<NX>() && b.mb == NX / 3 && b.W == 2 * (NX / 3) + 1;
+}
+
 #define TACAW_DISPATCH(N, FN, ...)       \
   switch (N) {                           \
     case 32: return FN<32>(__VA_ARGS__);     \
@@ -971,21 +983,33 @@ static cudaError_t prep(K kernel, int smem) {
 template <int NX>
 static cudaError_t splat_row_n(const Geo& g, const Band& b, const AtomRec* recs, const int* boffs, int64_t A,
                                int S, int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp,
-                               cudaStream_t st) {
+                               int static_band, cudaStream_t st) {
   if (s0 < 0 || sb < 1 || s0 + sb > S || nfs % sb != 0) return cudaErrorInvalidValue;
   if (2 * sk.half > SPREAD_MAX_W) return cudaErrorInvalidValue;
   const int smem = SplatSmem<NX>::BYTES;
+  const int nb = nfs * npair;
+  const dim3 grid = batch_grid(g.ny / SplatCfg<NX>::G, nb);
+  // not at 512 points, where the fixed-band build took more registers and measured 4% slower
+  if constexpr (std_band_built<NX>() && NX != 512) {
+    if (std_band<NX>(b, static_band)) {
+      cudaError_t e = prep(k_splat_row<NX, NX / 3>, smem);
+      if (e != cudaSuccess) return e;
+      k_splat_row<NX, NX / 3><<<grid, SplatCfg<NX>::THREADS, smem, st>>>(g, b, recs, boffs, (int)A, S, s0, sb,
+                                                                          npair, nb, sk, Bp);
+      return cudaGetLastError();
+    }
+  }
   cudaError_t e = prep(k_splat_row<NX>, smem);
   if (e != cudaSuccess) return e;
-  const int nb = nfs * npair;
-  k_splat_row<NX><<<batch_grid(g.ny / SplatCfg<NX>::G, nb), SplatCfg<NX>::THREADS, smem, st>>>(
-      g, b, recs, boffs, (int)A, S, s0, sb, npair, nb, sk, Bp);
+  k_splat_row<NX><<<grid, SplatCfg<NX>::THREADS, smem, st>>>(g, b, recs, boffs, (int)A, S, s0, sb, npair, nb, sk,
+                                                             Bp);
   return cudaGetLastError();
 }
 cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* boffs, int64_t A, int S,
-                             int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st) {
+                             int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, int static_band,
+                             cudaStream_t st) {
   if (g.ny % SPREAD_YB != 0) return cudaErrorInvalidValue;
-  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, boffs, A, S, s0, sb, nfs, npair, sk, Bp, st);
+  TACAW_DISPATCH(g.nx, splat_row_n, g, b, recs, boffs, A, S, s0, sb, nfs, npair, sk, Bp, static_band, st);
 }
 
 template <int NY>
@@ -1010,14 +1034,21 @@ cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const 
 
 template <int NX>
 static cudaError_t row_pot_out_n(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
-                                 float* V, float2* out, cudaStream_t st) {
-  k_row_pot_out<NX><<<batch_grid(g.ny / PotOutCfg<NX>::G, nfs), PotOutCfg<NX>::THREADS, PotOutCfg<NX>::SMEM, st>>>(
-      g, b, Ap, nfs, mode, sigma, V, out);
+                                 float* V, float2* out, int static_band, cudaStream_t st) {
+  const dim3 grid = batch_grid(g.ny / PotOutCfg<NX>::G, nfs);
+  if constexpr (std_band_built<NX>()) {
+    if (std_band<NX>(b, static_band)) {
+      k_row_pot_out<NX, NX / 3><<<grid, PotOutCfg<NX>::THREADS, PotOutCfg<NX>::SMEM, st>>>(g, b, Ap, nfs, mode,
+                                                                                           sigma, V, out);
+      return cudaGetLastError();
+    }
+  }
+  k_row_pot_out<NX><<<grid, PotOutCfg<NX>::THREADS, PotOutCfg<NX>::SMEM, st>>>(g, b, Ap, nfs, mode, sigma, V, out);
   return cudaGetLastError();
 }
 cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
-                               float* V, float2* out, cudaStream_t st) {
-  TACAW_DISPATCH(g.nx, row_pot_out_n, g, b, Ap, nfs, mode, sigma, V, out, st);
+                               float* V, float2* out, int static_band, cudaStream_t st) {
+  TACAW_DISPATCH(g.nx, row_pot_out_n, g, b, Ap, nfs, mode, sigma, V, out, static_band, st);
 }
 
 template <int NX>
@@ -1100,8 +1131,8 @@ static cudaError_t slice_row_n(const Geo& g, const Band& b, int first, int plane
   } while (0)
   // the later slices (all but one of S) with the standard band fixed at compile time
   constexpr int MB3 = NX / 3;
-  constexpr bool SPEC = fft_pow2(NX) && NX >= 128 && NX <= 1024;
-  const bool std_band = static_band && SPEC && b.mb == MB3 && b.W == 2 * MB3 + 1;
+  constexpr bool SPEC = std_band_built<NX>();
+  const bool std_band = tacaw::std_band<NX>(b, static_band);
 #define TACAW_SLICE_ROW_STD(TFU)                                                                                   \
   do {                                                                                                            \
     constexpr int SM = SliceRowSmem<NX, TFU>::BYTES;                                                              \

@@ -152,13 +152,14 @@ cudaError_t launch_sort_rows(const AtomRec* recs, const int* offs, int64_t A, in
 // Spreading row pass of slices [s0, s0 + sb) of nfs / sb frames (batch = (frame, slice, pair)),
 // from the row-sorted records and their row-block offsets.
 cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, const int* boffs, int64_t A, int S,
-                             int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, cudaStream_t st);
+                             int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, int static_band,
+                             cudaStream_t st);
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
                            float2* Ap, cudaStream_t st);
 // mode 0: store V; mode 1: t = exp(i sigma V), band-limit pass input (FFT_x, compact);
 // mode 2: t = exp(i sigma V) stored directly (no transmission band limit).
 cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
-                               float* V, float2* out, cudaStream_t st);
+                               float* V, float2* out, int static_band, cudaStream_t st);
 cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, int bandlimit, float sigma,
                           float2* out, cudaStream_t st);
 cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
@@ -172,7 +173,8 @@ cudaError_t launch_probe_row(const Geo& g, const Band& ap, const float2* Bpr, in
 // One slice s for n_waves = P * nfc waves; wave w = p * nfc + fl uses t[(fl * S + s)], full
 // rows, or with tfused the compact band-limit column-pass output, inverse-transformed in place.
 // static_band: the later slices use the kernel built for the standard 2/3 band of a square cell
-// (half-width NX / 3 fixed at compile time) when b is that band.
+// (half-width NX / 3 fixed at compile time) when b is that band (likewise in the spreading and
+// potential-output row passes).
 cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, int tfused, const float2* Apsi,
                              const float2* psi0, const float2* t, int S, int s, int P, int nfc, float plane_amp,
                              float2* Bpsi, int static_band, cudaStream_t st);

@@ -536,9 +536,9 @@ def test_run_is_deterministic(ctx, T):
 
 @pytest.mark.parametrize("grid,probe", [(128, False), (256, True), (512, False)])
 def test_fixed_band_row_pass_gives_the_same_bits(ctx, T, grid, probe):
-    """The later slices' row pass built for the standard 2/3 band (option static_band 1, used
-    here: square cells) and the one that reads the band at run time give the same bits; the
-    result is held to the oracle by the other parity tests."""
+    """The row passes built for the standard 2/3 band (spreading, potential output, later
+    slices; option static_band 1, used here: square cells) and the ones that read the band at
+    run time give the same bits; the result is held to the oracle by the other parity tests."""
     w = workloads.diamond_si(n_frames=3, grid=grid, n_slices=5, seed=47)
     if probe:
         w.alpha_mrad, w.probes = 25.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
