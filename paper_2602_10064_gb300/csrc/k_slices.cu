@@ -953,11 +953,12 @@ static cudaError_t prep(K kernel, int smem) {
 }
 
 // Row-pass kernels are also built for the standard 2/3 band of a square cell (half-width NX / 3
-// fixed at compile time) at these lengths; a launch uses that build when its band is that one
+// fixed at compile time) at these lengths (the powers of two of the configurations and the
+// minimal example's 1152); a launch uses that build when its band is that one
 // and the context option "static_band" is on.
 template <int NX>
 constexpr bool std_band_built() {
-  return fft_pow2(NX) && NX >= 128 && NX <= 1024;
+  return (fft_pow2(NX) && NX >= 128 && NX <= 1024) || NX == 1152;
 }
 template <int NX>
 bool std_band(const Band& b, int static_band) {

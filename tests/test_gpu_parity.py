@@ -534,18 +534,24 @@ def test_run_is_deterministic(ctx, T):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("grid,probe", [(128, False), (256, True), (512, False)])
+@pytest.mark.parametrize("grid,probe", [(128, False), (256, True), (512, False), (1152, True)])
 def test_fixed_band_row_pass_gives_the_same_bits(ctx, T, grid, probe):
     """The row passes built for the standard 2/3 band (spreading, potential output, later
     slices; option static_band 1, used here: square cells) and the ones that read the band at
     run time give the same bits; the result is held to the oracle by the other parity tests."""
-    w = workloads.diamond_si(n_frames=3, grid=grid, n_slices=5, seed=47)
-    if probe:
-        w.alpha_mrad, w.probes = 25.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
+    if grid == 1152:  # the minimal example's cell, whose band edge is exactly 384
+        w = workloads.minimal_example_si(n_frames=3, n_slices=5, n_scan=2 if probe else 0)
+    else:
+        w = workloads.diamond_si(n_frames=3, grid=grid, n_slices=5, seed=47)
+        if probe:
+            w.alpha_mrad, w.probes = 25.0, workloads.probe_grid(w.cell[0], w.cell[1], 2)
     ctx.load_form_factors(w.form_Z, w.form_coef)
     p, pr = T.params_of(w), T.probe_of(w)
     x = T.tacaw_band_points(ctx.h, p) % grid
-    assert x[x < grid // 2].max() == grid // 3  # the standard band: the fixed-band kernel runs
+    mb = x[x < grid // 2].max()
+    if grid % 3 == 0 and mb != grid // 3:
+        pytest.skip(f"the band edge rounds to {mb} here: the fixed-band kernel is not used")
+    assert mb == grid // 3  # the standard band: the fixed-band kernel runs
     pos, Z = dev(w.pos), dev(w.Z)
     try:
         ctx.set_option("static_band", 1)
