@@ -855,7 +855,7 @@ int slices(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const float2* t, 
       ProfScope ps(ctx, "slice_col", sc.st, rows * W8 + out, (double)P * nfc * g->band.W * (last ? 1 : 2) * fy);
       CK(launch_slice_col(geo, g->band, last, Bpsi, g->px, g->py,
                           last ? (float)(1.0 / std::sqrt((double)p.nx * p.ny)) : 1.0f / nq, P, nfc, F_total, f0,
-                          compact ? g->disc : nullptr, g->nsel, Apsi, psi_k, sc.st));
+                          compact ? g->disc : nullptr, g->nsel, Apsi, psi_k, (int)ctx->static_band, sc.st));
     }
   }
   return TACAW_OK;

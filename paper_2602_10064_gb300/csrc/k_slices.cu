@@ -848,7 +848,9 @@ __global__ void __launch_bounds__(SliceRowCfg<NX>::THREADS, minb_of<K_SLICE_ROW,
   store_row<NX, MB>(v, Bpsi + ((size_t)w * ny + y) * b.Wp, b, t);
 }
 
-template <int NY, bool LAST>
+// WPC > 0: the row stride of the compact columns (Wp) fixed at compile time (the standard band
+// of a square grid), so the strided loads and stores take immediate offsets; else Wp.
+template <int NY, bool LAST, int WPC = -1>
 __global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL, NY, SliceColCfg<NY>>())
     k_slice_col(Geo geo, Band b, const float2* __restrict__ Bpsi, const float2* __restrict__ px,
                 const float2* __restrict__ py, float scale, int nfc, int nwaves, int64_t F_total, int64_t f0,
@@ -860,14 +862,15 @@ __global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL,
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int w = batch_index();
   if (w >= nwaves) return;
+  const int Wp = WPC > 0 ? WPC : b.Wp;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C, CC::SH> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
-  const float2* src = Bpsi + (size_t)w * NY * b.Wp + cc;
+  const float2* src = Bpsi + (size_t)w * NY * Wp + cc;
   float2 v[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+  for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * Wp];
   fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
   const int nb = cc < b.W ? b.colnb[cc] : -1;
   const float2 pxc = cc < b.W ? px[cc] : make_float2(0.f, 0.f);
@@ -903,9 +906,9 @@ __global__ void __launch_bounds__(SliceColCfg<NY>::THREADS, minb_of<K_SLICE_COL,
     return;
   }
   fft<NY, +1, PL>(v, sm, idx, t, tw, sync);
-  float2* dst = Apsi + (size_t)w * NY * b.Wp + cc;
+  float2* dst = Apsi + (size_t)w * NY * Wp + cc;
 #pragma unroll
-  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
+  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * Wp] = v[e];
 }
 
 // ============================================================================================
@@ -963,6 +966,11 @@ constexpr bool std_band_built() {
 template <int NX>
 bool std_band(const Band& b, int static_band) {
   return static_band && std_band_built<NX>() && b.mb == NX / 3 && b.W == 2 * (NX / 3) + 1;
+}
+// Padded row stride of the compact columns for that band (as make_band pads W).
+constexpr int std_band_wp(int n) {
+  const int w = 2 * (n / 3) + 1, up = (w + 31) / 32 * 32, wp = up < 32 ? 32 : up;
+  return wp > n ? n : wp;
 }
 
 #define TACAW_DISPATCH(N, FN, ...)       \
@@ -1171,11 +1179,23 @@ cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, 
 template <int NY>
 static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
                                const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
-                               const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st) {
+                               const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, int static_band,
+                               cudaStream_t st) {
   const int nw = P * nfc;
   using CC = SliceColCfg<NY>;
   const dim3 grid = batch_grid(col_blocks(b, CC::C), nw);
   constexpr int TH = CC::THREADS, SM = CC::SMEM;
+  // the later slices of a square grid with the standard band: row stride fixed at compile time
+  if constexpr (std_band_built<NY>()) {
+    constexpr int WP = std_band_wp(NY);
+    if (!last && g.nx == NY && b.Wp == WP && std_band<NY>(b, static_band)) {
+      cudaError_t e = prep(k_slice_col<NY, false, WP>, SM);
+      if (e != cudaSuccess) return e;
+      k_slice_col<NY, false, WP><<<grid, TH, SM, st>>>(g, b, Bpsi, px, py, scale, nfc, nw, F_total, f0, disc, nsel,
+                                                       Apsi, psi_k);
+      return cudaGetLastError();
+    }
+  }
   cudaError_t e = last ? prep(k_slice_col<NY, true>, SM) : prep(k_slice_col<NY, false>, SM);
   if (e != cudaSuccess) return e;
   if (last)
@@ -1188,9 +1208,10 @@ static cudaError_t slice_col_n(const Geo& g, const Band& b, int last, const floa
 }
 cudaError_t launch_slice_col(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
                              const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
-                             const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st) {
+                             const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, int static_band,
+                             cudaStream_t st) {
   TACAW_DISPATCH(g.ny, slice_col_n, g, b, last, Bpsi, px, py, scale, P, nfc, F_total, f0, disc, nsel, Apsi, psi_k,
-                 st);
+                 static_band, st);
 }
 
 cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot, const double* coef_slots,

@@ -184,7 +184,8 @@ cudaError_t launch_slice_row(const Geo& g, const Band& b, int first, int plane, 
 // number disc[y].y.
 cudaError_t launch_slice_col(const Geo& g, const Band& b, int last, const float2* Bpsi, const float2* px,
                              const float2* py, float scale, int P, int nfc, int64_t F_total, int64_t f0,
-                             const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, cudaStream_t st);
+                             const int2* disc, int64_t nsel, float2* Apsi, float2* psi_k, int static_band,
+                             cudaStream_t st);
 // mtab[pair][ny][Wp] = C M(k) (f_2p(|k|) - i f_2p+1(|k|)) / (Phi_x Phi_y), FP64 evaluation.
 cudaError_t launch_build_mtab(const Geo& g, const Band& b, int npair, int nslot, const double* coef_slots,
                               const double* phix, const double* phiy, double Lx, double Ly, double pref,
