@@ -665,7 +665,7 @@ int potential_block(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const Bi
   {
     ProfScope ps(ctx, "col_pot", st, (double)nfs * (g->npair + 1) * ny * W8 + (double)g->npair * ny * W8,
                  (double)nfs * (g->npair + 1) * g->band.W * fy);
-    CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, st));
+    CK(launch_col_pot(geo, g->band, Bp, g->mtab, g->npair, nfs, Ap, (int)ctx->static_band, st));
   }
   return TACAW_OK;
 }
@@ -750,7 +750,8 @@ int transmission_from(tacaw_ctx* ctx, const tacaw_params& p, GeoCache* g, const 
   }
   {
     ProfScope ps(ctx, "col_t", sc.st, 2.0 * nfs * p.ny * W8, 2.0 * nfs * g->band.W * fy);
-    CK(launch_col_t(geo, g->band, Bt, nfs, 1.0f / ((float)p.nx * (float)p.ny), At, sc.st));
+    CK(launch_col_t(geo, g->band, Bt, nfs, 1.0f / ((float)p.nx * (float)p.ny), At, (int)ctx->static_band,
+                    sc.st));
   }
   if (!compact) {
     ProfScope ps(ctx, "row_tout", sc.st, row * (W8 + 8.0 * p.nx), row * fx);

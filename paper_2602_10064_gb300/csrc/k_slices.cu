@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(SplatCfg<NX>::THREADS, minb_of<K_SPLAT_ROW, NX
 }
 
 // Column pass of the potential: per (f, s), sum over species pairs of mtab * FFT_y, then IFFT_y.
-template <int NY, bool ONE>
+template <int NY, bool ONE, int WPC = -1>
 __global__ void __launch_bounds__(ColPotCfg<NY>::THREADS, minb_of<K_COL_POT, NY, ColPotCfg<NY>>())
     k_col_pot(Geo geo, Band b, const float2* __restrict__ Bp, const float2* __restrict__ mtab, int npair, int nbatch,
               float2* __restrict__ Ap) {
@@ -556,42 +556,43 @@ __global__ void __launch_bounds__(ColPotCfg<NY>::THREADS, minb_of<K_COL_POT, NY,
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
   if (fs >= nbatch) return;
+  const int Wp = WPC > 0 ? WPC : b.Wp;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C, CC::SH> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
   if constexpr (ONE) {
     // one species pair: no accumulator held across the transforms
-    const float2* src = Bp + (size_t)fs * NY * b.Wp + cc;
+    const float2* src = Bp + (size_t)fs * NY * Wp + cc;
     float2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+    for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * Wp];
     fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
     const float2* m = mtab + cc;
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
+    for (int e = 0; e < E; ++e) v[e] = cmul(m[(size_t)(t + T * e) * Wp], v[e]);
     fft<NY, +1, PL>(v, sm, idx, t, tw, sync);
-    float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
+    float2* dst = Ap + (size_t)fs * NY * Wp + cc;
 #pragma unroll
-    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
+    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * Wp] = v[e];
   } else {
     float2 acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = make_float2(0.f, 0.f);
     for (int pr = 0; pr < npair; ++pr) {
-      const float2* src = Bp + (size_t)(fs * npair + pr) * NY * b.Wp + cc;
+      const float2* src = Bp + (size_t)(fs * npair + pr) * NY * Wp + cc;
       float2 v[E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+      for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * Wp];
       fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
-      const float2* m = mtab + (size_t)pr * NY * b.Wp + cc;
+      const float2* m = mtab + (size_t)pr * NY * Wp + cc;
 #pragma unroll
-      for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * b.Wp], v[e]);
+      for (int e = 0; e < E; ++e) acc[e] = acc[e] + cmul(m[(size_t)(t + T * e) * Wp], v[e]);
     }
     fft<NY, +1, PL>(acc, sm, idx, t, tw, sync);
-    float2* dst = Ap + (size_t)fs * NY * b.Wp + cc;
+    float2* dst = Ap + (size_t)fs * NY * Wp + cc;
 #pragma unroll
-    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = acc[e];
+    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * Wp] = acc[e];
   }
 }
 
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(RowVtCfg<NX>::THREADS, minb_of<K_ROW_VT, NX, R
 }
 
 // Column pass of the band limit: FFT_y, * M * scale, IFFT_y.
-template <int NY>
+template <int NY, int WPC = -1>
 __global__ void __launch_bounds__(ColTCfg<NY>::THREADS, minb_of<K_COL_T, NY, ColTCfg<NY>>())
     k_col_t(Geo geo, Band b, const float2* __restrict__ Bt, int nbatch, float scale, float2* __restrict__ At) {
   using CC = ColTCfg<NY>;
@@ -677,14 +678,15 @@ __global__ void __launch_bounds__(ColTCfg<NY>::THREADS, minb_of<K_COL_T, NY, Col
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int fs = batch_index();
   if (fs >= nbatch) return;
+  const int Wp = WPC > 0 ? WPC : b.Wp;
   const int c = threadIdx.x % C, t = threadIdx.x / C, cc = blockIdx.x * C + c;
   const ColIdx<C, CC::SH> idx{c};
   const BlockSync sync;
   const float2* tw = geo.tw + tw_offset(NY);
-  const float2* src = Bt + (size_t)fs * NY * b.Wp + cc;
+  const float2* src = Bt + (size_t)fs * NY * Wp + cc;
   float2 v[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * b.Wp];
+  for (int e = 0; e < E; ++e) v[e] = src[(size_t)(t + T * e) * Wp];
   fft<NY, -1, PL>(v, sm, idx, t, tw, sync);
   const int nb = cc < b.W ? b.colnb[cc] : -1;
 #pragma unroll
@@ -693,9 +695,9 @@ __global__ void __launch_bounds__(ColTCfg<NY>::THREADS, minb_of<K_COL_T, NY, Col
     v[e] = (abs(n) <= nb) ? scale * v[e] : make_float2(0.f, 0.f);
   }
   fft<NY, +1, PL>(v, sm, idx, t, tw, sync);
-  float2* dst = At + (size_t)fs * NY * b.Wp + cc;
+  float2* dst = At + (size_t)fs * NY * Wp + cc;
 #pragma unroll
-  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * b.Wp] = v[e];
+  for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) * Wp] = v[e];
 }
 
 // Row pass out of the band limit: IFFT_x -> t (full row).
@@ -1023,10 +1025,23 @@ cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, c
 
 template <int NY>
 static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
-                             float2* Ap, cudaStream_t st) {
+                             float2* Ap, int static_band, cudaStream_t st) {
   using CC = ColPotCfg<NY>;
   const dim3 grid = batch_grid(col_blocks(b, CC::C), nfs);
   cudaError_t e;
+  if constexpr (std_band_built<NY>()) {
+    constexpr int WP = std_band_wp(NY);
+    if (g.nx == NY && b.Wp == WP && std_band<NY>(b, static_band)) {
+      if (npair == 1) {
+        if ((e = prep(k_col_pot<NY, true, WP>, CC::SMEM)) != cudaSuccess) return e;
+        k_col_pot<NY, true, WP><<<grid, CC::THREADS, CC::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
+      } else {
+        if ((e = prep(k_col_pot<NY, false, WP>, CC::SMEM)) != cudaSuccess) return e;
+        k_col_pot<NY, false, WP><<<grid, CC::THREADS, CC::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
+      }
+      return cudaGetLastError();
+    }
+  }
   if (npair == 1) {
     if ((e = prep(k_col_pot<NY, true>, CC::SMEM)) != cudaSuccess) return e;
     k_col_pot<NY, true><<<grid, CC::THREADS, CC::SMEM, st>>>(g, b, Bp, mtab, npair, nfs, Ap);
@@ -1037,8 +1052,8 @@ static cudaError_t col_pot_n(const Geo& g, const Band& b, const float2* Bp, cons
   return cudaGetLastError();
 }
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
-                           float2* Ap, cudaStream_t st) {
-  TACAW_DISPATCH(g.ny, col_pot_n, g, b, Bp, mtab, npair, nfs, Ap, st);
+                           float2* Ap, int static_band, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, col_pot_n, g, b, Bp, mtab, npair, nfs, Ap, static_band, st);
 }
 
 template <int NX>
@@ -1074,8 +1089,17 @@ cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, 
 
 template <int NY>
 static cudaError_t col_t_n(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
-                           cudaStream_t st) {
+                           int static_band, cudaStream_t st) {
   using CC = ColTCfg<NY>;
+  if constexpr (std_band_built<NY>()) {
+    constexpr int WP = std_band_wp(NY);
+    if (g.nx == NY && b.Wp == WP && std_band<NY>(b, static_band)) {
+      const cudaError_t e = prep(k_col_t<NY, WP>, CC::SMEM);
+      if (e != cudaSuccess) return e;
+      k_col_t<NY, WP><<<batch_grid(col_blocks(b, CC::C), nfs), CC::THREADS, CC::SMEM, st>>>(g, b, Bt, nfs, scale, At);
+      return cudaGetLastError();
+    }
+  }
   const cudaError_t e = prep(k_col_t<NY>, CC::SMEM);
   if (e != cudaSuccess) return e;
   k_col_t<NY><<<batch_grid(col_blocks(b, CC::C), nfs), CC::THREADS, CC::SMEM, st>>>(g, b, Bt, nfs,
@@ -1083,8 +1107,8 @@ static cudaError_t col_t_n(const Geo& g, const Band& b, const float2* Bt, int nf
   return cudaGetLastError();
 }
 cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
-                         cudaStream_t st) {
-  TACAW_DISPATCH(g.ny, col_t_n, g, b, Bt, nfs, scale, At, st);
+                         int static_band, cudaStream_t st) {
+  TACAW_DISPATCH(g.ny, col_t_n, g, b, Bt, nfs, scale, At, static_band, st);
 }
 
 template <int NX>

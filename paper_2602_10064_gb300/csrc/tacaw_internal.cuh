@@ -155,7 +155,7 @@ cudaError_t launch_splat_row(const Geo& g, const Band& b, const AtomRec* recs, c
                              int s0, int sb, int nfs, int npair, SpreadKernel sk, float2* Bp, int static_band,
                              cudaStream_t st);
 cudaError_t launch_col_pot(const Geo& g, const Band& b, const float2* Bp, const float2* mtab, int npair, int nfs,
-                           float2* Ap, cudaStream_t st);
+                           float2* Ap, int static_band, cudaStream_t st);
 // mode 0: store V; mode 1: t = exp(i sigma V), band-limit pass input (FFT_x, compact);
 // mode 2: t = exp(i sigma V) stored directly (no transmission band limit).
 cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, int nfs, int mode, float sigma,
@@ -163,7 +163,7 @@ cudaError_t launch_row_pot_out(const Geo& g, const Band& b, const float2* Ap, in
 cudaError_t launch_row_vt(const Geo& g, const Band& b, const float* V, int nfs, int bandlimit, float sigma,
                           float2* out, cudaStream_t st);
 cudaError_t launch_col_t(const Geo& g, const Band& b, const float2* Bt, int nfs, float scale, float2* At,
-                         cudaStream_t st);
+                         int static_band, cudaStream_t st);
 cudaError_t launch_row_tout(const Geo& g, const Band& b, const float2* At, int nfs, float2* t, cudaStream_t st);
 // chi (nullable): exp(-i chi(k)) over [ny][ap.Wp]
 cudaError_t launch_probe_col(const Geo& g, const Band& ap, const float2* ex, const float2* ey, const float2* chi,
